@@ -1,0 +1,120 @@
+// Internal helpers shared by the library's translation units: status and error
+// messages, the device allocator hooks, launch accounting and the grid handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtdmor.h"
+
+namespace fdtdmor {
+
+// ------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+fdtd_status cuda_fail(cudaError_t e, const char *what);
+
+#define FDTD_CHECK_CUDA(expr)                                 \
+  do {                                                        \
+    cudaError_t e__ = (expr);                                 \
+    if (e__ != cudaSuccess) return ::fdtdmor::cuda_fail(e__, #expr); \
+  } while (0)
+
+#define FDTD_CHECK(expr)                     \
+  do {                                       \
+    fdtd_status s__ = (expr);                \
+    if (s__ != FDTD_OK) return s__;          \
+  } while (0)
+
+#define FDTD_REQUIRE(cond, ...)              \
+  do {                                       \
+    if (!(cond)) {                           \
+      ::fdtdmor::set_error(__VA_ARGS__);     \
+      return FDTD_EINVAL;                    \
+    }                                        \
+  } while (0)
+
+// After a kernel launch: count it and surface launch-configuration errors.
+fdtd_status after_launch(const char *name);
+
+// ------------------------------------------------------------ memory
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// Device buffer owned by a handle.
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  fdtd_status alloc(size_t n, cudaStream_t s);
+  void release(cudaStream_t s);
+  template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ------------------------------------------------------------ physics constants
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4.0e-7 * kPi;
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+
+// ------------------------------------------------------------ grid handle
+// Per-axis tables (precision T), packed in one buffer, each of length n_axis:
+//   rd   = 1/d[i]                         (primal spacing)
+//   rdd  = 2/(d[i-1]+d[i]), 0 at i = 0     (dual spacing)
+//   wlo  = d[i-1]/(d[i-1]+d[i]), whi = d[i]/(d[i-1]+d[i])   (cell weights)
+enum AxisTable { AX_RD = 0, AX_RDD = 1, AX_WLO = 2, AX_WHI = 3, AX_COUNT = 4 };
+
+// Source/probe entry in the per-tile lists used by the fused kernels.
+struct PortEntry {
+  int32_t k;      // plane
+  int16_t lx, ly; // local coordinates in the tile's extended region
+  int16_t comp;   // 0..2
+  int16_t pad;
+  int32_t port;   // column of B / row of C
+  double w;       // weight
+};
+
+struct TileLists {
+  int tx = 0, ty = 0;       // tile shape the lists were built for
+  int ntx = 0, nty = 0;
+  DevBuf src_ptr, src;      // CSR over xy-tiles, entries sorted by k
+  DevBuf prb_ptr, prb;
+  int64_t nsrc = 0, nprb = 0;
+};
+
+struct HostPort {
+  int comp;
+  std::vector<int64_t> cell;
+  std::vector<double> w;
+};
+
+}  // namespace fdtdmor
+
+struct fdtd_grid {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t nc = 0;
+  fdtd_prec prec = FDTD_F32;
+  int elem = 4;                 // bytes per field value
+  int nmat = 0;
+  int id_bytes = 1;             // 1 (uint8) or 2 (uint16)
+  bool homog_h = true;          // every material has the same mu_r, sig_m
+  std::vector<double> dx, dy, dz, eps_r, mu_r, sig_e, sig_m;
+  std::vector<uint8_t> pec;
+  std::vector<uint16_t> used_mats;
+  std::vector<fdtdmor::HostPort> ports, probes;
+  double cfl = 0;
+
+  fdtdmor::DevBuf fields[2];    // ping-pong: 6*nc values each
+  int cur = 0;                  // buffer holding the current state
+  fdtdmor::DevBuf mat;          // per-cell material id
+  fdtdmor::DevBuf axis;         // AX_COUNT * (nx + ny + nz) values of the field type
+  fdtdmor::DevBuf mtab;         // per-material properties in the field type: eps, sig, mu, sigm, pec
+  fdtdmor::DevBuf mraw;         // the same table in double, relative eps/mu (source of ctab)
+  fdtdmor::DevBuf ctab;         // per-material coefficients for the cached dt: ca, cb, da, db
+  double ctab_dt = -1;
+  fdtdmor::TileLists lists;
+  fdtdmor::DevBuf u_stage, y_stage;  // device staging for fdtd_step_host
+  cudaStream_t create_stream = nullptr;
+};

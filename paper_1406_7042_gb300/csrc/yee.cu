@@ -1,0 +1,383 @@
+// A2: full-order Yee leap-frog of Eq. (matrix) / Eq. (MNAform), one fused
+// kernel per time step.
+//
+// Each CTA owns an xy tile of TX x TY cells and marches up a chunk of z planes.
+// For plane k it stages H^{n+1/2}[k] (tile plus a one-cell halo) and the cell
+// material ids in shared memory, computes E^{n+1}[k] on the tile plus its +x/+y
+// halo (the halo values are recomputed redundantly instead of exchanged), adds
+// the sources, then computes H^{n+3/2}[k-1] from E^{n+1}[k-1] and E^{n+1}[k].
+// Reads E^n, H^{n+1/2} from one buffer and writes E^{n+1}, H^{n+3/2} to the
+// other (ping-pong), so every field value is read once and written once per
+// step: 48 B (f32) or 96 B (f64) of field traffic per cell-update.
+//
+// Per edge, (Ca, Cb) come from the per-material table when the cells around
+// the edge share a material, else from the area-weighted eps/sigma of those
+// cells (the non-uniform, inhomogeneous reading of Sec. II-A).
+#include <algorithm>
+
+#include "common.cuh"
+#include "grid_internal.cuh"
+
+namespace fdtdmor {
+
+constexpr int YTX = 32, YTY = 8, YNT = YTX * YTY;
+constexpr int YEX = YTX + 1, YEY = YTY + 1;   // E region: tile + high halo
+constexpr int YHX = YTX + 2, YHY = YTY + 2;   // H / id region: tile + both halos
+
+template <typename T, typename ID>
+struct YeeArgs {
+  int nx, ny, nz, kchunk;
+  int64_t nc;
+  const T *__restrict__ Ein;   // 3 components, stride nc
+  const T *__restrict__ Hin;
+  T *__restrict__ Eout;
+  T *__restrict__ Hout;
+  const ID *__restrict__ mat;
+  const T *__restrict__ ax;    // axis tables (AX_COUNT x (nx+ny+nz))
+  const T *__restrict__ mtab;  // eps, sig, mu, sigm, pec (5 x nmat)
+  const T *__restrict__ ctab;  // ca, cb, da, db (4 x nmat)
+  int nmat;
+  T inv_dt;
+  const int32_t *__restrict__ src_ptr;
+  const PortEntry *__restrict__ src;
+  const T *__restrict__ u;     // row of this step: u[port]
+  const int32_t *__restrict__ prb_ptr;
+  const PortEntry *__restrict__ prb;
+  T *__restrict__ y;           // row of this step: y[probe]
+};
+
+template <typename T>
+__device__ __forceinline__ T axv(const T *ax, int ntot, int table, int idx) {
+  return __ldg(ax + table * ntot + idx);
+}
+
+// (Ca, Cb) of an E edge from the four cells around it (c00: lo/lo, c10: hi/lo,
+// c01: lo/hi, c11: hi/hi along the two transverse axes) and their weights.
+template <typename T, typename ID>
+__device__ __forceinline__ void e_coef(const YeeArgs<T, ID> &a, ID c00, ID c10, ID c01, ID c11,
+                                       T wa_lo, T wa_hi, T wb_lo, T wb_hi, T &ca, T &cb) {
+  if (c00 == c10 && c00 == c01 && c00 == c11) {
+    ca = __ldg(a.ctab + c00);
+    cb = __ldg(a.ctab + a.nmat + c00);
+    return;
+  }
+  const T *pec = a.mtab + 4 * a.nmat;
+  if (__ldg(pec + c00) != T(0) || __ldg(pec + c10) != T(0) || __ldg(pec + c01) != T(0) ||
+      __ldg(pec + c11) != T(0)) {
+    ca = T(0);
+    cb = T(0);
+    return;
+  }
+  const T *eps = a.mtab, *sig = a.mtab + a.nmat;
+  T w00 = wa_lo * wb_lo, w10 = wa_hi * wb_lo, w01 = wa_lo * wb_hi, w11 = wa_hi * wb_hi;
+  T e = w00 * __ldg(eps + c00) + w10 * __ldg(eps + c10) + w01 * __ldg(eps + c01) + w11 * __ldg(eps + c11);
+  T s = w00 * __ldg(sig + c00) + w10 * __ldg(sig + c10) + w01 * __ldg(sig + c01) + w11 * __ldg(sig + c11);
+  T ae = e * a.inv_dt;
+  cb = T(1) / (ae + T(0.5) * s);
+  ca = (ae - T(0.5) * s) * cb;
+}
+
+// (Da, Db) of an H edge from the two cells its dual edge crosses.
+template <typename T, typename ID>
+__device__ __forceinline__ void h_coef(const YeeArgs<T, ID> &a, ID c0, ID c1, T w0, T w1, T &da,
+                                       T &db) {
+  if (c0 == c1) {
+    da = __ldg(a.ctab + 2 * a.nmat + c0);
+    db = __ldg(a.ctab + 3 * a.nmat + c0);
+    return;
+  }
+  const T *mu = a.mtab + 2 * a.nmat, *sgm = a.mtab + 3 * a.nmat;
+  T m = w0 * __ldg(mu + c0) + w1 * __ldg(mu + c1);
+  T s = w0 * __ldg(sgm + c0) + w1 * __ldg(sgm + c1);
+  T am = m * a.inv_dt;
+  db = T(1) / (am + T(0.5) * s);
+  da = (am - T(0.5) * s) * db;
+}
+
+template <typename T, typename ID>
+struct YeeSmem {
+  T H[3][3][YHY][YHX];   // H^{n+1/2}, three plane slots (k % 3)
+  T E[2][3][YEY][YEX];   // E^{n+1}, two plane slots (k & 1)
+  ID M[4][YHY][YHX];     // material ids, four plane slots (k & 3)
+  int rng[2];            // this plane's source range
+};
+
+// (Ca, Cb) of E component c at extended-region position (lx, ly) of plane k.
+template <typename T, typename ID>
+__device__ __forceinline__ void e_coef_at(const YeeArgs<T, ID> &a, const YeeSmem<T, ID> &sm, int c,
+                                          int lx, int ly, int i, int j, int k, T &ca, T &cb) {
+  const int ntot = a.nx + a.ny + a.nz;
+  const int hx = lx + 1, hy = ly + 1;
+  const int mk = k & 3, mkm = (k + 3) & 3;  // planes k and k-1
+  if (c == 0) {
+    if (j == 0 || k == 0) { ca = cb = T(0); return; }
+    e_coef(a, sm.M[mkm][hy - 1][hx], sm.M[mkm][hy][hx], sm.M[mk][hy - 1][hx], sm.M[mk][hy][hx],
+           axv(a.ax, ntot, AX_WLO, a.nx + j), axv(a.ax, ntot, AX_WHI, a.nx + j),
+           axv(a.ax, ntot, AX_WLO, a.nx + a.ny + k), axv(a.ax, ntot, AX_WHI, a.nx + a.ny + k), ca, cb);
+  } else if (c == 1) {
+    if (i == 0 || k == 0) { ca = cb = T(0); return; }
+    e_coef(a, sm.M[mkm][hy][hx - 1], sm.M[mkm][hy][hx], sm.M[mk][hy][hx - 1], sm.M[mk][hy][hx],
+           axv(a.ax, ntot, AX_WLO, i), axv(a.ax, ntot, AX_WHI, i),
+           axv(a.ax, ntot, AX_WLO, a.nx + a.ny + k), axv(a.ax, ntot, AX_WHI, a.nx + a.ny + k), ca, cb);
+  } else {
+    if (i == 0 || j == 0) { ca = cb = T(0); return; }
+    e_coef(a, sm.M[mk][hy - 1][hx - 1], sm.M[mk][hy - 1][hx], sm.M[mk][hy][hx - 1], sm.M[mk][hy][hx],
+           axv(a.ax, ntot, AX_WLO, i), axv(a.ax, ntot, AX_WHI, i),
+           axv(a.ax, ntot, AX_WLO, a.nx + j), axv(a.ax, ntot, AX_WHI, a.nx + j), ca, cb);
+  }
+}
+
+template <typename T, typename ID, bool HOMOG_H>
+__global__ void __launch_bounds__(YNT) yee_fused_kernel(YeeArgs<T, ID> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  YeeSmem<T, ID> &sm = *reinterpret_cast<YeeSmem<T, ID> *>(smem_raw);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * YTX + tx;
+  const int i0 = blockIdx.x * YTX, j0 = blockIdx.y * YTY;
+  const int k0 = blockIdx.z * a.kchunk;
+  if (k0 >= a.nz) return;
+  const int k1 = min(a.nz, k0 + a.kchunk);
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int64_t nc = a.nc;
+  const int ntot = nx + ny + nz;
+  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+  const int s_beg = a.src_ptr[tile], s_end = a.src_ptr[tile + 1];
+  const int p_beg = a.prb_ptr[tile], p_end = a.prb_ptr[tile + 1];
+
+  auto load_plane = [&](int k) {  // H^{n+1/2}[k] and ids of plane k into their slots
+    const int hs = ((k % 3) + 3) % 3, ms = k & 3;
+    for (int t = tid; t < YHX * YHY; t += YNT) {
+      const int lx = t % YHX, ly = t / YHX;
+      const int i = i0 - 1 + lx, j = j0 - 1 + ly;
+      const bool in = (k >= 0) && (k < nz) && (i >= 0) && (i < nx) && (j >= 0) && (j < ny);
+      const int64_t idx = in ? ((int64_t)k * ny + j) * nx + i : 0;
+      sm.H[hs][0][ly][lx] = in ? a.Hin[idx] : T(0);
+      sm.H[hs][1][ly][lx] = in ? a.Hin[nc + idx] : T(0);
+      sm.H[hs][2][ly][lx] = in ? a.Hin[2 * nc + idx] : T(0);
+      sm.M[ms][ly][lx] = in ? a.mat[idx] : ID(0);
+    }
+  };
+
+  int sp = s_beg;
+  load_plane(k0 - 1);
+  for (int k = k0; k <= k1; ++k) {
+    const bool live = k < nz;
+    if (live) load_plane(k);
+    if (tid == 0) {
+      while (sp < s_end && a.src[sp].k < k) ++sp;
+      int sq = sp;
+      while (sq < s_end && a.src[sq].k == k) ++sq;
+      sm.rng[0] = sp;
+      sm.rng[1] = sq;
+    }
+    __syncthreads();  // (A) plane k staged
+    const int r0 = sm.rng[0], r1 = sm.rng[1];
+    const int es = k & 1, esp = (k + 1) & 1;
+    const int hs = k % 3, hsp = (k + 2) % 3;
+    // ---- E^{n+1}[k] on tile + high halo
+    for (int t = tid; t < YEX * YEY; t += YNT) {
+      const int lx = t % YEX, ly = t / YEX;
+      const int i = i0 + lx, j = j0 + ly;
+      T ex = T(0), ey = T(0), ez = T(0);
+      if (live && i < nx && j < ny) {
+        const int hx = lx + 1, hy = ly + 1;
+        const int64_t idx = ((int64_t)k * ny + j) * nx + i;
+        const T rxd = axv(a.ax, ntot, AX_RDD, i);
+        const T ryd = axv(a.ax, ntot, AX_RDD, nx + j);
+        const T rzd = axv(a.ax, ntot, AX_RDD, nx + ny + k);
+        T ca, cb;
+        // (curl H)_x = dHz/dy - dHy/dz
+        e_coef_at(a, sm, 0, lx, ly, i, j, k, ca, cb);
+        ex = ca * a.Ein[idx] + cb * ((sm.H[hs][2][hy][hx] - sm.H[hs][2][hy - 1][hx]) * ryd -
+                                     (sm.H[hs][1][hy][hx] - sm.H[hsp][1][hy][hx]) * rzd);
+        // (curl H)_y = dHx/dz - dHz/dx
+        e_coef_at(a, sm, 1, lx, ly, i, j, k, ca, cb);
+        ey = ca * a.Ein[nc + idx] + cb * ((sm.H[hs][0][hy][hx] - sm.H[hsp][0][hy][hx]) * rzd -
+                                          (sm.H[hs][2][hy][hx] - sm.H[hs][2][hy][hx - 1]) * rxd);
+        // (curl H)_z = dHy/dx - dHx/dy
+        e_coef_at(a, sm, 2, lx, ly, i, j, k, ca, cb);
+        ez = ca * a.Ein[2 * nc + idx] + cb * ((sm.H[hs][1][hy][hx] - sm.H[hs][1][hy][hx - 1]) * rxd -
+                                              (sm.H[hs][0][hy][hx] - sm.H[hs][0][hy - 1][hx]) * ryd);
+      }
+      sm.E[es][0][ly][lx] = ex;
+      sm.E[es][1][ly][lx] = ey;
+      sm.E[es][2][ly][lx] = ez;
+    }
+    __syncthreads();  // (B)
+    // ---- sources of plane k: E -= Cb w u   (B = -w V_e, divided by V_e)
+    if (r1 > r0) {
+      for (int s = r0 + tid; s < r1; s += YNT) {
+        const PortEntry pe = a.src[s];
+        const int i = i0 + pe.lx, j = j0 + pe.ly;
+        if (i < nx && j < ny) {
+          T ca, cb;
+          e_coef_at(a, sm, pe.comp, pe.lx, pe.ly, i, j, k, ca, cb);
+          atomicAdd(&sm.E[es][pe.comp][pe.ly][pe.lx], -cb * (T)pe.w * a.u[pe.port]);
+        }
+      }
+      __syncthreads();  // (C)
+    }
+    const int i = i0 + tx, j = j0 + ty;
+    const bool own = i < nx && j < ny;
+    if (k < k1) {
+      if (own) {
+        const int64_t idx = ((int64_t)k * ny + j) * nx + i;
+        a.Eout[idx] = sm.E[es][0][ty][tx];
+        a.Eout[nc + idx] = sm.E[es][1][ty][tx];
+        a.Eout[2 * nc + idx] = sm.E[es][2][ty][tx];
+      }
+      for (int s = p_beg + tid; s < p_end; s += YNT) {
+        const PortEntry pe = a.prb[s];
+        if (pe.k == k) atomicAdd(&a.y[pe.port], (T)pe.w * sm.E[es][pe.comp][pe.ly][pe.lx]);
+      }
+    }
+    // ---- H^{n+3/2}[k-1] on the tile
+    if (k > k0 && own) {
+      const int kk = k - 1;
+      const int64_t idx = ((int64_t)kk * ny + j) * nx + i;
+      const int hx = tx + 1, hy = ty + 1;
+      const T rdx = axv(a.ax, ntot, AX_RD, i);
+      const T rdy = axv(a.ax, ntot, AX_RD, nx + j);
+      const T rdz = axv(a.ax, ntot, AX_RD, nx + ny + kk);
+      const T(*E0)[YEY][YEX] = sm.E[esp];  // E^{n+1}[kk]
+      const T(*E1)[YEY][YEX] = sm.E[es];   // E^{n+1}[kk+1]
+      T da[3], db[3];
+      if (HOMOG_H) {
+        da[0] = da[1] = da[2] = __ldg(a.ctab + 2 * a.nmat);
+        db[0] = db[1] = db[2] = __ldg(a.ctab + 3 * a.nmat);
+      } else {
+        const int mk = kk & 3, mkm = (kk + 3) & 3;
+        h_coef(a, sm.M[mk][hy][hx - 1], sm.M[mk][hy][hx], axv(a.ax, ntot, AX_WLO, i),
+               axv(a.ax, ntot, AX_WHI, i), da[0], db[0]);
+        h_coef(a, sm.M[mk][hy - 1][hx], sm.M[mk][hy][hx], axv(a.ax, ntot, AX_WLO, nx + j),
+               axv(a.ax, ntot, AX_WHI, nx + j), da[1], db[1]);
+        h_coef(a, sm.M[mkm][hy][hx], sm.M[mk][hy][hx], axv(a.ax, ntot, AX_WLO, nx + ny + kk),
+               axv(a.ax, ntot, AX_WHI, nx + ny + kk), da[2], db[2]);
+      }
+      // mu dHx/dt = -(dEz/dy - dEy/dz)
+      T hxv = da[0] * sm.H[hsp][0][hy][hx] -
+              db[0] * ((E0[2][ty + 1][tx] - E0[2][ty][tx]) * rdy - (E1[1][ty][tx] - E0[1][ty][tx]) * rdz);
+      // mu dHy/dt = -(dEx/dz - dEz/dx)
+      T hyv = da[1] * sm.H[hsp][1][hy][hx] -
+              db[1] * ((E1[0][ty][tx] - E0[0][ty][tx]) * rdz - (E0[2][ty][tx + 1] - E0[2][ty][tx]) * rdx);
+      // mu dHz/dt = -(dEy/dx - dEx/dy)
+      T hzv = da[2] * sm.H[hsp][2][hy][hx] -
+              db[2] * ((E0[1][ty][tx + 1] - E0[1][ty][tx]) * rdx - (E0[0][ty + 1][tx] - E0[0][ty][tx]) * rdy);
+      a.Hout[idx] = (i == 0) ? T(0) : hxv;        // normal H on the x walls
+      a.Hout[nc + idx] = (j == 0) ? T(0) : hyv;
+      a.Hout[2 * nc + idx] = (kk == 0) ? T(0) : hzv;
+    }
+  }
+}
+
+template <typename T, typename ID, bool HH>
+static fdtd_status launch_yee_t(fdtd_grid *g, const void *u_row, void *y_row, int kchunk,
+                                cudaStream_t s) {
+  YeeArgs<T, ID> a;
+  a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.kchunk = kchunk; a.nc = g->nc;
+  const T *in = g->fields[g->cur].as<T>();
+  T *out = g->fields[g->cur ^ 1].as<T>();
+  a.Ein = in; a.Hin = in + 3 * g->nc;
+  a.Eout = out; a.Hout = out + 3 * g->nc;
+  a.mat = g->mat.as<ID>();
+  a.ax = g->axis.as<T>();
+  a.mtab = g->mtab.as<T>();
+  a.ctab = g->ctab.as<T>();
+  a.nmat = g->nmat;
+  a.inv_dt = (T)(1.0 / g->ctab_dt);
+  a.src_ptr = g->lists.src_ptr.as<int32_t>();
+  a.src = g->lists.src.as<PortEntry>();
+  a.u = static_cast<const T *>(u_row);
+  a.prb_ptr = g->lists.prb_ptr.as<int32_t>();
+  a.prb = g->lists.prb.as<PortEntry>();
+  a.y = static_cast<T *>(y_row);
+  dim3 grid(g->lists.ntx, g->lists.nty, (g->nz + kchunk - 1) / kchunk);
+  dim3 block(YTX, YTY);
+  size_t smem = sizeof(YeeSmem<T, ID>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(yee_fused_kernel<T, ID, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  yee_fused_kernel<T, ID, HH><<<grid, block, smem, s>>>(a);
+  return after_launch("yee_fused_kernel");
+}
+
+static fdtd_status launch_yee(fdtd_grid *g, const void *u_row, void *y_row, int kchunk,
+                              cudaStream_t s) {
+  if (g->prec == FDTD_F64) {
+    if (g->id_bytes == 1)
+      return g->homog_h ? launch_yee_t<double, uint8_t, true>(g, u_row, y_row, kchunk, s)
+                        : launch_yee_t<double, uint8_t, false>(g, u_row, y_row, kchunk, s);
+    return g->homog_h ? launch_yee_t<double, uint16_t, true>(g, u_row, y_row, kchunk, s)
+                      : launch_yee_t<double, uint16_t, false>(g, u_row, y_row, kchunk, s);
+  }
+  if (g->id_bytes == 1)
+    return g->homog_h ? launch_yee_t<float, uint8_t, true>(g, u_row, y_row, kchunk, s)
+                      : launch_yee_t<float, uint8_t, false>(g, u_row, y_row, kchunk, s);
+  return g->homog_h ? launch_yee_t<float, uint16_t, true>(g, u_row, y_row, kchunk, s)
+                    : launch_yee_t<float, uint16_t, false>(g, u_row, y_row, kchunk, s);
+}
+
+int choose_kchunk(const fdtd_grid *g, int ntiles) {
+  const int target = 152 * 4;
+  int nchunks = std::max(1, (target + ntiles - 1) / ntiles);
+  nchunks = std::min(nchunks, std::max(1, g->nz / 4));
+  return (g->nz + nchunks - 1) / nchunks;
+}
+
+fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
+                    int reset_fields, cudaStream_t s) {
+  FDTD_REQUIRE(dt > 0, "dt must be > 0");
+  FDTD_REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  FDTD_REQUIRE(nsteps == 0 || g->ports.empty() || u, "u is required when the grid has sources");
+  FDTD_REQUIRE(nsteps == 0 || g->probes.empty() || y, "y is required when the grid has probes");
+  FDTD_CHECK(ensure_coef_table(g, dt, s));
+  FDTD_CHECK(build_tile_lists(g, YTX, YTY, s));
+  if (reset_fields) {
+    FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)6 * g->nc * g->elem, s));
+  }
+  const int m = (int)g->ports.size(), p = (int)g->probes.size();
+  if (p && nsteps) FDTD_CHECK_CUDA(cudaMemsetAsync(y, 0, (size_t)nsteps * p * g->elem, s));
+  const int kchunk = choose_kchunk(g, g->lists.ntx * g->lists.nty);
+  for (int64_t n = 0; n < nsteps; ++n) {
+    const char *ur = u ? static_cast<const char *>(u) + (size_t)n * m * g->elem : nullptr;
+    char *yr = y ? static_cast<char *>(y) + (size_t)n * p * g->elem : nullptr;
+    FDTD_CHECK(launch_yee(g, ur, yr, kchunk, s));
+    g->cur ^= 1;
+  }
+  return FDTD_OK;
+}
+
+}  // namespace fdtdmor
+
+using namespace fdtdmor;
+
+extern "C" {
+
+fdtd_status fdtd_step(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
+                      int reset_fields, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g, "fdtd_step: NULL grid");
+  return yee_run(g, dt, nsteps, u, y, reset_fields, (cudaStream_t)stream);
+}
+
+fdtd_status fdtd_step_host(fdtd_grid *g, double dt, int64_t nsteps, const void *u_host,
+                           void *y_host, int reset_fields, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g, "fdtd_step_host: NULL grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ub = (size_t)nsteps * g->ports.size() * g->elem;
+  const size_t yb = (size_t)nsteps * g->probes.size() * g->elem;
+  FDTD_REQUIRE(ub == 0 || u_host, "u_host is required when the grid has sources");
+  FDTD_REQUIRE(yb == 0 || y_host, "y_host is required when the grid has probes");
+  if (ub) {
+    FDTD_CHECK(g->u_stage.alloc(ub, s));
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(g->u_stage.ptr, u_host, ub, cudaMemcpyHostToDevice, s));
+  }
+  if (yb) FDTD_CHECK(g->y_stage.alloc(yb, s));
+  FDTD_CHECK(yee_run(g, dt, nsteps, ub ? g->u_stage.ptr : nullptr, yb ? g->y_stage.ptr : nullptr,
+                     reset_fields, s));
+  if (yb) FDTD_CHECK_CUDA(cudaMemcpyAsync(y_host, g->y_stage.ptr, yb, cudaMemcpyDeviceToHost, s));
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of the C ABI in include/fdtdmor.h.
+
+Argument marshalling only: every step of the method runs in libfdtdmor.so.
+Device memory for the library's handles comes from PyTorch's caching
+allocator (installed through fdtd_set_allocator); u, y and other caller
+buffers are torch tensors passed by pointer on the current torch stream.
+If the library is missing this module raises on first use; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import sys
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdtdmor.so")
+
+FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ENOCONV, FDTD_EUNSTABLE, FDTD_ETIMEOUT = range(7)
+FDTD_F64, FDTD_F32 = 0, 1
+STATUS_NAMES = {0: "FDTD_OK", 1: "FDTD_EINVAL", 2: "FDTD_ENOMEM", 3: "FDTD_ECUDA",
+                4: "FDTD_ENOCONV", 5: "FDTD_EUNSTABLE", 6: "FDTD_ETIMEOUT"}
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.POINTER(C.c_double)), ("dy", C.POINTER(C.c_double)),
+                ("dz", C.POINTER(C.c_double)), ("nmat", C.c_int),
+                ("eps_r", C.POINTER(C.c_double)), ("mu_r", C.POINTER(C.c_double)),
+                ("sig_e", C.POINTER(C.c_double)), ("sig_m", C.POINTER(C.c_double)),
+                ("pec", C.POINTER(C.c_uint8)), ("mat_id", C.POINTER(C.c_uint16)),
+                ("prec", C.c_int)]
+
+
+class PortDesc(C.Structure):
+    _fields_ = [("comp", C.c_int), ("n", C.c_int64), ("cell", C.POINTER(C.c_int64)),
+                ("w", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+_alloc_cbs = None
+_live = None  # weak set of open handles, closed at interpreter exit
+
+
+def _close_all():
+    if _live is not None:
+        for h in list(_live):
+            try:
+                h.close()
+            except Exception:
+                pass
+
+
+def _track(obj):
+    global _live
+    import atexit
+    import weakref
+    if _live is None:
+        _live = weakref.WeakSet()
+        atexit.register(_close_all)
+    _live.add(obj)
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("fdtd_set_allocator", C.c_int, [ALLOC_FN, FREE_FN]),
+    ("fdtd_last_error", C.c_char_p, []),
+    ("fdtd_grid_create", C.c_int, [C.POINTER(GridDesc), C.c_int, C.POINTER(PortDesc), C.c_int,
+                                   C.POINTER(PortDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("fdtd_grid_destroy", C.c_int, [C.c_void_p]),
+    ("fdtd_cfl_dt", C.c_double, [C.c_void_p]),
+    ("fdtd_step", C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                            C.c_void_p]),
+    ("fdtd_step_host", C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.c_void_p]),
+    ("fdtd_fields_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("fdtd_fields_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("fdtd_launch_count", C.c_int64, [C.c_int]),
+]
+
+
+def declared_symbols() -> List[str]:
+    """Function names declared in include/fdtdmor.h (parsed from the header)."""
+    import re
+    hdr = open(os.path.join(_HERE, "..", "include", "fdtdmor.h")).read()
+    return sorted(set(re.findall(r"FDTD_API\s+[\w\s\*]+?\b((?:fdtd|mor)_\w+)\s*\(", hdr)))
+
+
+def lib(install_allocator: bool = True):
+    """Load libfdtdmor.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FdtdError(FDTD_ECUDA, f"{LIB_PATH} not built: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = L
+        if install_allocator:
+            _install_torch_allocator()
+    return _lib
+
+
+def _install_torch_allocator():
+    global _alloc_cbs
+    import torch
+    if not torch.cuda.is_available():
+        return
+
+    def _alloc(nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:  # out of memory -> NULL, the library reports FDTD_ENOMEM
+            return None
+
+    def _free(ptr, stream):
+        if ptr:
+            torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _lib.fdtd_set_allocator(*_alloc_cbs)
+
+
+def check(status: int):
+    if status != FDTD_OK:
+        raise FdtdError(status, lib().fdtd_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensor must be CUDA and contiguous"
+    return int(t.data_ptr())
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(lib().fdtd_launch_count(1 if reset else 0))
+
+
+class Grid:
+    """Owns an fdtd_grid handle built from a workloads.GridSpec."""
+
+    def __init__(self, spec, prec: str = "f32", stream=None):
+        import torch
+        self.spec = spec
+        self.prec = prec
+        self.dtype = torch.float64 if prec == "f64" else torch.float32
+        self.np_dtype = np.float64 if prec == "f64" else np.float32
+        L = lib()
+        keep = []
+
+        def arr(a, ct, dt):
+            a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+            keep.append(a)
+            return a.ctypes.data_as(C.POINTER(ct))
+
+        d = GridDesc()
+        d.nx, d.ny, d.nz = spec.nx, spec.ny, spec.nz
+        d.dx = arr(spec.dx, C.c_double, np.float64)
+        d.dy = arr(spec.dy, C.c_double, np.float64)
+        d.dz = arr(spec.dz, C.c_double, np.float64)
+        d.nmat = spec.nmat
+        d.eps_r = arr(spec.eps_r, C.c_double, np.float64)
+        d.mu_r = arr(spec.mu_r, C.c_double, np.float64)
+        d.sig_e = arr(spec.sig_e, C.c_double, np.float64)
+        d.sig_m = arr(spec.sig_m, C.c_double, np.float64)
+        d.pec = arr(spec.pec, C.c_uint8, np.uint8)
+        d.mat_id = arr(spec.mat_id, C.c_uint16, np.uint16)
+        d.prec = FDTD_F64 if prec == "f64" else FDTD_F32
+
+        def ports(lst):
+            P = (PortDesc * max(1, len(lst)))()
+            for n, p in enumerate(lst):
+                cells = (np.asarray(p.k, np.int64) * spec.ny + np.asarray(p.j, np.int64)) * spec.nx \
+                    + np.asarray(p.i, np.int64)
+                P[n].comp = int(p.comp)
+                P[n].n = int(cells.size)
+                P[n].cell = arr(cells, C.c_int64, np.int64)
+                P[n].w = arr(p.w, C.c_double, np.float64)
+            return P
+
+        P = ports(spec.ports)
+        Q = ports(spec.probes)
+        h = C.c_void_p()
+        check(L.fdtd_grid_create(C.byref(d), len(spec.ports), P, len(spec.probes), Q,
+                                 _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.m = len(spec.ports)
+        self.p = len(spec.probes)
+        _track(self)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fdtd_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cfl_dt(self) -> float:
+        return float(lib().fdtd_cfl_dt(self.h))
+
+    def step(self, dt: float, u, y=None, reset: bool = False, stream=None, nsteps: int = None):
+        """Run len(u) (or nsteps) steps; u: (nsteps, m) device tensor; returns y (nsteps, p)."""
+        import torch
+        n = int(nsteps if nsteps is not None else u.shape[0])
+        if y is None and self.p:
+            y = torch.empty((n, self.p), dtype=self.dtype, device="cuda")
+        check(lib().fdtd_step(self.h, float(dt), n, _dptr(u) if self.m else None,
+                              _dptr(y) if self.p else None, 1 if reset else 0, _stream_ptr(stream)))
+        return y
+
+    def step_host(self, dt: float, u_host, y_host, reset: bool = False, stream=None):
+        """Host-buffer variant: u_host, y_host are (pinned) CPU tensors."""
+        n = int(u_host.shape[0])
+        check(lib().fdtd_step_host(self.h, float(dt), n, int(u_host.data_ptr()) if self.m else None,
+                                   int(y_host.data_ptr()) if self.p else None, 1 if reset else 0,
+                                   _stream_ptr(stream)))
+        return y_host
+
+    def fields(self, stream=None):
+        """(6, nz, ny, nx) tensor copy of Ex, Ey, Ez, Hx, Hy, Hz."""
+        import torch
+        s = self.spec
+        out = torch.empty((6, s.nz, s.ny, s.nx), dtype=self.dtype, device="cuda")
+        check(lib().fdtd_fields_get(self.h, _dptr(out), _stream_ptr(stream)))
+        return out
+
+    def set_fields(self, f, stream=None):
+        f = f.contiguous()
+        check(lib().fdtd_fields_set(self.h, _dptr(f), _stream_ptr(stream)))

@@ -1,0 +1,167 @@
+"""Parity of the CUDA Yee leap-frog (fdtd_step, through the C ABI) with the
+FP64 oracle: whole fields and probes on small ragged grids, the FP64 10^3
+cavity in full, and light-cone samples of the full-size graded cavity and
+metascreen grids in the launch configuration the benchmark uses."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import yee  # noqa: E402
+from paper_1406_7042_gb300 import fdtdmor as F  # noqa: E402
+from paper_1406_7042_gb300 import workloads as W  # noqa: E402
+from tests.helpers import drive, oracle_state_to_arrays, ragged_grid, subgrid  # noqa: E402
+
+# FP32 tolerance of the full-order path: 2e-4 relative L2 on probe waveforms.
+TOL_F32_PROBE = 2e-4
+TOL_F64 = 1e-9
+
+
+def _run_gpu(grid, prec, dt, u, reset=True):
+    g = F.Grid(grid, prec)
+    ut = torch.tensor(u, dtype=g.dtype, device="cuda")
+    y = g.step(dt, ut, reset=reset)
+    f = g.fields()
+    torch.cuda.synchronize()
+    return g, (y.cpu().numpy() if y is not None else None), f.cpu().numpy()
+
+
+def _run_oracle(grid, dt, u):
+    s = yee.assemble(grid)
+    y, x, _ = yee.Stepper(s, dt).run(u)
+    return s, y, oracle_state_to_arrays(s, x)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_cfl_matches_oracle():
+    for grid in (W.config1().grid, W.config2().grid, ragged_grid()):
+        g = F.Grid(grid, "f32")
+        assert abs(g.cfl_dt() - yee.cfl_dt(grid)) <= 1e-15 * yee.cfl_dt(grid)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("many", [False, True])
+def test_ragged_graded_lossy_parity(prec, many):
+    grid = ragged_grid(many_materials=many)
+    dt = 0.95 * yee.cfl_dt(grid)
+    u = drive(grid, dt, 160)
+    g, yg, fg = _run_gpu(grid, prec, dt, u)
+    s, yo, fo = _run_oracle(grid, dt, u)
+    if prec == "f64":
+        assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
+        assert np.max(np.abs(yg - yo)) <= TOL_F64 * np.abs(yo).max()
+    else:
+        for c in range(6):
+            assert _rel(fg[c], fo[c]) <= 1e-4, c
+        assert _rel(yg, yo) <= TOL_F32_PROBE
+    # removed unknowns (PEC / walls) are exactly zero on the GPU
+    for c in range(3):
+        assert np.all(fg[c][~s.e_mask[c]] == 0)
+        assert np.all(fg[3 + c][~s.h_mask[c]] == 0)
+
+
+def test_config1_f64_full_run():
+    wl = W.config1()
+    dt = wl.s_ref * yee.cfl_dt(wl.grid)
+    u = W.excitation(wl.grid, wl.f0, wl.bw, dt, wl.nsteps_ref)
+    _, yg, fg = _run_gpu(wl.grid, "f64", dt, u)
+    _, yo, fo = _run_oracle(wl.grid, dt, u)
+    assert np.max(np.abs(yg - yo)) <= TOL_F64 * np.abs(yo).max()
+    assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
+
+
+def test_state_continues_across_calls_and_host_variant():
+    grid = ragged_grid(seed=7)
+    dt = 0.9 * yee.cfl_dt(grid)
+    u = drive(grid, dt, 90)
+    g = F.Grid(grid, "f32")
+    ut = torch.tensor(u, dtype=torch.float32, device="cuda")
+    y1 = g.step(dt, ut[:40], reset=True)
+    y2 = g.step(dt, ut[40:], reset=False)
+    f_split = g.fields().cpu().numpy()
+    yall = g.step(dt, ut, reset=True)
+    f_once = g.fields().cpu().numpy()
+    torch.cuda.synchronize()
+    # multi-edge probes are summed with atomics: equal up to summation order
+    yref = yall.cpu().numpy()
+    assert np.allclose(torch.cat([y1, y2]).cpu().numpy(), yref, rtol=1e-6, atol=1e-7 * np.abs(yref).max())
+    assert np.array_equal(f_split, f_once)
+    uh = torch.tensor(u, dtype=torch.float32).pin_memory()
+    yh = torch.empty((90, g.p), dtype=torch.float32).pin_memory()
+    g.step_host(dt, uh, yh, reset=True)
+    assert np.allclose(yh.numpy(), yref, rtol=1e-6, atol=1e-7 * np.abs(yref).max())
+
+
+def test_degenerate_grids_and_empty_ports():
+    for (nx, ny, nz) in [(1, 1, 1), (1, 5, 3), (33, 1, 2), (2, 9, 1)]:
+        eps, mu, se, sm, pec = W.vacuum_table()
+        grid = W.GridSpec(nx, ny, nz, np.full(nx, 1e-3), np.full(ny, 1e-3), np.full(nz, 1e-3),
+                          eps, mu, se, sm, pec, np.zeros((nz, ny, nx), np.uint16))
+        g = F.Grid(grid, "f32")
+        y = g.step(1e-13, torch.zeros((5, 0), device="cuda"), nsteps=5)
+        assert y is None
+        f = g.fields()
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(f).item() == 0
+    grid = ragged_grid(seed=9)
+    g = F.Grid(grid, "f32")
+    y = g.step(0.5 * g.cfl_dt(), torch.zeros((0, g.m), device="cuda"), nsteps=0)
+    assert y.shape == (0, g.p)
+
+
+def test_invalid_arguments_are_rejected():
+    grid = ragged_grid(seed=3)
+    g = F.Grid(grid, "f32")
+    with pytest.raises(F.FdtdError) as e:
+        g.step(-1.0, torch.zeros((3, g.m), device="cuda"))
+    assert e.value.status == F.FDTD_EINVAL
+    bad = ragged_grid(seed=3)
+    bad.mat_id = bad.mat_id.copy()
+    bad.mat_id[0, 0, 0] = bad.nmat
+    with pytest.raises(F.FdtdError):
+        F.Grid(bad, "f32")
+
+
+def _light_cone_check(grid, prec, dt, nsteps, centres, half):
+    """GPU run on the full grid vs the oracle on a sub-grid around each centre:
+    after n steps a field value depends only on data within n+1 cells, so the
+    sub-grid's own PEC walls (n+2 cells away) cannot reach the sampled block."""
+    u = drive(grid, dt, nsteps, f0=10e9, bw=10e9)
+    _, yg, fg = _run_gpu(grid, prec, dt, u)
+    r = nsteps + 2
+    for (ci, cj, ck) in centres:
+        lo = (max(0, ci - half - r), max(0, cj - half - r), max(0, ck - half - r))
+        hi = (min(grid.nx, ci + half + r + 1), min(grid.ny, cj + half + r + 1), min(grid.nz, ck + half + r + 1))
+        sg = subgrid(grid, lo, hi)
+        us = u[:, :len(sg.ports)] if sg.ports else np.zeros((nsteps, 0))
+        s = yee.assemble(sg)
+        _, xs, _ = yee.Stepper(s, dt).run(us if sg.ports else np.zeros((nsteps, 0)))
+        fo = oracle_state_to_arrays(s, xs)
+        sl = (slice(None), slice(ck - half - lo[2], ck + half + 1 - lo[2]),
+              slice(cj - half - lo[1], cj + half + 1 - lo[1]), slice(ci - half - lo[0], ci + half + 1 - lo[0]))
+        gsl = (slice(None), slice(ck - half, ck + half + 1), slice(cj - half, cj + half + 1),
+               slice(ci - half, ci + half + 1))
+        a, b = fg[gsl], fo[sl]
+        scale = max(np.abs(fo).max(), 1e-30)
+        assert np.max(np.abs(a - b)) <= (1e-4 if prec == "f32" else 1e-10) * scale
+
+
+def test_full_size_graded_cavity_light_cone():
+    wl = W.config2()
+    grid = wl.grid
+    dt = wl.s_ref * yee.cfl_dt(grid)
+    p = grid.ports[0]
+    centres = [(int(p.i[0]), int(p.j[0]), int(p.k[0])), (32, 32, 32), (60, 3, 40)]
+    _light_cone_check(grid, "f32", dt, 12, centres, 3)
+
+
+def test_full_size_metascreen_light_cone():
+    wl = W.config5()
+    grid = wl.grid
+    dt = wl.s_ref * yee.cfl_dt(grid)
+    centres = [(192, 192, 9), (70, 300, 31), (383 - 5, 5, 8)]
+    _light_cone_check(grid, "f32", dt, 10, centres, 3)
