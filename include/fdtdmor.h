@@ -130,9 +130,111 @@ FDTD_API fdtd_status fdtd_step_host(fdtd_grid *grid, double dt, int64_t nsteps, 
 FDTD_API fdtd_status fdtd_fields_get(const fdtd_grid *grid, void *fields6, fdtd_stream_t stream);
 FDTD_API fdtd_status fdtd_fields_set(fdtd_grid *grid, const void *fields6, fdtd_stream_t stream);
 
+/* Per-edge material values the reduction kernels use (A1): 12 arrays of nc
+ * values of the grid's type, contiguous -- eps (F/m, 0 on dead edges: walls
+ * and PEC) and sigma_e (S/m) for Ex, Ey, Ez, then mu (H/m, 0 for H normal to
+ * a wall) and sigma_m for Hx, Hy, Hz -- copied to the device buffer dst. */
+FDTD_API fdtd_status fdtd_edge_props_get(fdtd_grid *grid, void *dst, fdtd_stream_t stream);
+
 /* Kernel launches issued by the calling thread since the last reset (for
  * launch accounting).  fdtd_launch_count(1) returns the count and resets it. */
 FDTD_API int64_t fdtd_launch_count(int reset);
+
+
+/* ------------------------------------------------------------------------
+ * Structure-preserving reduction (SPRIM, Sec. II-C) and reduced stepping.
+ * ------------------------------------------------------------------------ */
+typedef struct mor_basis mor_basis;
+typedef struct mor_model mor_model;
+
+/* Arithmetic of the block Gram-Schmidt (CGS2) products of the basis build:
+ * the grid's own type, or tensor-core TF32 / BF16 inputs with FP32
+ * accumulation (FDTD_F32 grids only).  Gram norms and R factors are FP64. */
+typedef enum { MOR_ORTH_NATIVE = 0, MOR_ORTH_TF32 = 1, MOR_ORTH_BF16 = 2 } mor_orth;
+
+/* Krylov solver of the shifted Schur-complement systems.  The paper uses
+ * conjugate gradient squared (Sec. IV-B).  AUTO picks it for FDTD_F64 grids
+ * and BiCGSTAB for FDTD_F32 grids, where the squared residual polynomial of
+ * CGS amplifies rounding on the complex-shifted (indefinite) systems.  Both
+ * are right-preconditioned by the Jacobi diagonal, and convergence is
+ * confirmed on the true residual b - S x, with restarts when the recursively
+ * updated residual has drifted from it. */
+typedef enum { MOR_SOLVER_AUTO = 0, MOR_SOLVER_CGS = 1, MOR_SOLVER_BICGSTAB = 2 } mor_solver;
+
+typedef struct {
+  int q;              /* requested columns of V1 and of V2 (Sec. II-C "N~")        */
+  int L;              /* expansion points l = -L..L of Eq. (distrib)                */
+  double M;           /* radius of the arc, 1.1 in Sec. IV-A                         */
+  double fmax;        /* highest frequency of interest (Hz)                          */
+  double dt0;         /* time step the basis is built at (> 0)                       */
+  int include_center; /* 1: l = -L..L; 0: only the pair z = M e^{+-j 2 pi fmax dt0}   */
+  double tol;         /* conjugate-gradient-squared residual limit (Sec. IV-B: 1e-4)  */
+  int maxit;          /* iteration cap per shifted solve                             */
+  double defl_tol;    /* drop a vector whose norm after CGS2 is below defl_tol x before */
+  mor_orth orth;
+  mor_solver solver;
+} mor_opts;
+
+/* Fill *opts with M = 1.1, L = 2, tol = 1e-4, maxit = 20000, defl_tol = 1e-8
+ * (FP64) -- q, fmax and dt0 must still be set by the caller. */
+FDTD_API fdtd_status mor_opts_default(mor_opts *opts);
+
+/* A3-A5 -- SPRIM basis (Sec. II-C, Sec. IV): for each expansion point
+ * z_l = M exp(j 2 pi (l/L) fmax dt0), l = 0..L (conjugate points implied), a
+ * block-Arnoldi chain of k = q/((2L+1) m) block moments
+ * v_0 = A_l^{-1} B, v_j = A_l^{-1} (R+F) v_{j-1}, A_l = z_l (R+F) - (R-F), each
+ * shifted solve by conjugate gradient squared on the Schur complement
+ * A11 - A12 A22^{-1} A21 (Eqs. (reduced_linear_system_solution1/2)), Jacobi
+ * preconditioned, to a normalised residual <= tol; then Re/Im of every
+ * chain vector is split into its E and H parts and each pool is
+ * orthonormalised with CGS2 and deflation -> V1 (3nc x q1), V2 (3nc x q2).
+ * Returns FDTD_ENOCONV if a solve hit maxit (the basis is still returned). */
+FDTD_API fdtd_status mor_build_basis(fdtd_grid *grid, const mor_opts *opts, fdtd_stream_t stream,
+                                     mor_basis **out);
+/* Columns kept, worst iteration count and worst final relative residual. */
+FDTD_API fdtd_status mor_basis_info(const mor_basis *basis, int *q1, int *q2, int *max_iters,
+                                    double *max_resid);
+/* Copy V1 (which = 1) or V2 (which = 2), column-major [q][3 nc] of the grid's
+ * type, to the device buffer dst. */
+FDTD_API fdtd_status mor_basis_get(const mor_basis *basis, int which, void *dst, fdtd_stream_t stream);
+FDTD_API fdtd_status mor_basis_destroy(mor_basis *basis);
+
+/* A6 -- projection, Eq. (R_and_Freduced): D~eps = V1^T D_eps V1,
+ * D~se = V1^T D_se V1, D~mu = V2^T D_mu V2, D~sm = V2^T D_sm V2,
+ * K~ = V1^T K V2, B~ = V^T B, C~ = C V, accumulated in FP64. */
+FDTD_API fdtd_status mor_project(fdtd_grid *grid, const mor_basis *basis, fdtd_stream_t stream,
+                                 mor_model **out);
+
+/* A7 -- perturbation of Sec. III-A for time step dt: with D~eps = Le Le^T,
+ * D~mu = Lm Lm^T (Cholesky; equivalent to the symmetric roots), SVD
+ * Le^{-1} K~ Lm^{-T} = U S W^T, sigma' = sigma if sigma < gamma 2/dt else
+ * gamma 2/dt, K~' = Le U S' W^T Lm^T; then the step matrices of the reduced
+ * leap-frog at dt.  *n_clipped receives the number of clipped values (host
+ * pointer, may be NULL).  Synchronises the stream. */
+FDTD_API fdtd_status mor_perturb(mor_model *model, double dt, double gamma, int *n_clipped,
+                                 fdtd_stream_t stream);
+
+/* A8 -- reduced leap-frog, Eq. (reducedMNAform) in block form, nsteps steps at
+ * the dt of the last mor_perturb, in one persistent kernel:
+ * e <- Pe e - Qe h + be u^{n+1}, h <- Ph h + Qh e + bh u^{n+1}, y^n = C~ e.
+ * u: device [nsteps][m], y: device [nsteps][p] (grid type). */
+FDTD_API fdtd_status mor_run(mor_model *model, int64_t nsteps, const void *u, void *y,
+                             int reset_state, fdtd_stream_t stream);
+
+/* Reduced matrices to host, row-major doubles.  which: 0 D~eps, 1 D~se,
+ * 2 D~mu, 3 D~sm, 4 K~, 5 K~' (after mor_perturb), 6 B~_E, 7 C~_E,
+ * 8 singular values sigma before clipping (1 x q).  rows/cols receive the
+ * shape; host_out may be NULL to query it.  Synchronises the stream. */
+FDTD_API fdtd_status mor_model_get(const mor_model *model, int which, double *host_out, int *rows,
+                                   int *cols, fdtd_stream_t stream);
+FDTD_API fdtd_status mor_model_destroy(mor_model *model);
+
+/* A9 -- relative L2 error ||y_red - y_ref[sub]|| / ||y_ref[sub]|| over the
+ * common samples: y_red [n][p], y_ref rows offset + i*stride, i < n (device,
+ * type prec).  *err receives the value (host).  Synchronises the stream. */
+FDTD_API fdtd_status mor_compare(const void *y_red, const void *y_ref, int64_t n, int64_t stride,
+                                 int64_t offset, int p, fdtd_prec prec, double *err,
+                                 fdtd_stream_t stream);
 
 #ifdef __cplusplus
 }

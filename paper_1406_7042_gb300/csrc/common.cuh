@@ -116,5 +116,7 @@ struct fdtd_grid {
   double ctab_dt = -1;
   fdtdmor::TileLists lists;
   fdtdmor::DevBuf u_stage, y_stage;  // device staging for fdtd_step_host
+  fdtdmor::DevBuf eprops;       // per-edge eps, sig (E) and mu, sgm (H), 4 x 3 x nc (reduction kernels)
+  bool eprops_ready = false;
   cudaStream_t create_stream = nullptr;
 };

@@ -297,6 +297,7 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->lists.prb.release(s);
   g->u_stage.release(s);
   g->y_stage.release(s);
+  g->eprops.release(s);
   cudaStreamSynchronize(s);
   delete g;
   return FDTD_OK;

@@ -1,0 +1,1044 @@
+// A3-A5: Krylov basis of the SPRIM reduction (Sec. II-C) with complex frequency
+// hopping (Sec. IV-A, Eq. (distrib)) and the shifted solves of Sec. IV-B.
+//
+// All operators act on the per-volume form of Eq. (matrix) (each E row divided
+// by its edge volume, each H row by its dual volume), in which -K/V_e is the
+// discrete curl of Ampere's law and -K^T/V_h the curl of Faraday's law:
+//   (R+F) v:  r1 = (eps/dt + sig/2) v1,  r2 = curlE(v1) + (mu/dt + sgm/2) v2
+//   A(z) = z(R+F) - (R-F):  a11 = (z-1) eps/dt + (z+1) sig/2,
+//                           a22 = (z-1) mu/dt + (z+1) sgm/2,
+//   Schur complement  S x1 = a11 x1 + z curlH(curlE(x1)/a22),
+//   right-hand side   b^  = r1 + curlH(r2/a22),    x2 = (r2 - z curlE(x1))/a22.
+// Row scaling leaves the Krylov subspaces of A^{-1}(R+F) unchanged.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <vector>
+
+#include "grid_internal.cuh"
+#include "mor_common.cuh"
+#include "mor_internal.cuh"
+
+namespace fdtdmor {
+
+constexpr int MB = 256;  // threads per block of the elementwise / stencil kernels
+
+// ------------------------------------------------------------------ edge props
+template <typename T, typename ID>
+__global__ void edge_props_kernel(Geo<T> g, const ID *__restrict__ mat, const T *__restrict__ mtab,
+                                  int nmat, T *__restrict__ out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= g.nc) return;
+  const int nx = g.nx, ny = g.ny;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((int64_t)nx * ny));
+  const T *eps = mtab, *sig = mtab + nmat, *mu = mtab + 2 * nmat, *sgm = mtab + 3 * nmat, *pec = mtab + 4 * nmat;
+  const int nt = g.ntot();
+  auto W = [&](int axis, int idx, bool hi) { return __ldg(g.ax + (hi ? AX_WHI : AX_WLO) * nt + g.off(axis) + idx); };
+  auto M = [&](int ii, int jj, int kk) { return (int)mat[g.id(ii, jj, kk)]; };
+  const int64_t nc = g.nc;
+  // E edges: area-weighted mean over the four cells around the edge
+  for (int c = 0; c < 3; ++c) {
+    int a0, a1, i0, i1;  // transverse axes and indices
+    bool wall;
+    if (c == 0) { a0 = 1; a1 = 2; i0 = j; i1 = k; wall = (j == 0 || k == 0); }
+    else if (c == 1) { a0 = 0; a1 = 2; i0 = i; i1 = k; wall = (i == 0 || k == 0); }
+    else { a0 = 0; a1 = 1; i0 = i; i1 = j; wall = (i == 0 || j == 0); }
+    T e = 0, s = 0;
+    if (!wall) {
+      bool anypec = false;
+      for (int b1 = 0; b1 < 2; ++b1)
+        for (int b0 = 0; b0 < 2; ++b0) {
+          int ii = i, jj = j, kk = k;
+          int d0 = b0 - 1, d1 = b1 - 1;
+          if (a0 == 0) ii += d0; else jj += d0;
+          if (a1 == 1) jj += d1; else kk += d1;
+          const int m = M(ii, jj, kk);
+          const T w = W(a0, i0, b0) * W(a1, i1, b1);
+          anypec |= __ldg(pec + m) != T(0);
+          e += w * __ldg(eps + m);
+          s += w * __ldg(sig + m);
+        }
+      if (anypec) { e = 0; s = 0; }
+    }
+    out[EP_EPS * 3 * nc + c * nc + n] = e;
+    out[EP_SIG * 3 * nc + c * nc + n] = s;
+  }
+  // H edges: length-weighted mean over the two cells the dual edge crosses
+  for (int c = 0; c < 3; ++c) {
+    const int idx = c == 0 ? i : (c == 1 ? j : k);
+    T m_ = 0, s = 0;
+    if (idx > 0) {
+      const int m0 = c == 0 ? M(i - 1, j, k) : (c == 1 ? M(i, j - 1, k) : M(i, j, k - 1));
+      const int m1 = M(i, j, k);
+      const T w0 = W(c, idx, false), w1 = W(c, idx, true);
+      m_ = w0 * __ldg(mu + m0) + w1 * __ldg(mu + m1);
+      s = w0 * __ldg(sgm + m0) + w1 * __ldg(sgm + m1);
+    }
+    out[EP_MU * 3 * nc + c * nc + n] = m_;
+    out[EP_SGM * 3 * nc + c * nc + n] = s;
+  }
+}
+
+fdtd_status ensure_edge_props(fdtd_grid *g, cudaStream_t s) {
+  if (g->eprops_ready) return FDTD_OK;
+  FDTD_CHECK(g->eprops.alloc((size_t)12 * g->nc * g->elem, s));
+  const int bl = (int)((g->nc + MB - 1) / MB);
+  if (g->prec == FDTD_F64) {
+    if (g->id_bytes == 1)
+      edge_props_kernel<double, uint8_t><<<bl, MB, 0, s>>>(make_geo<double>(g), g->mat.as<uint8_t>(), g->mtab.as<double>(), g->nmat, g->eprops.as<double>());
+    else
+      edge_props_kernel<double, uint16_t><<<bl, MB, 0, s>>>(make_geo<double>(g), g->mat.as<uint16_t>(), g->mtab.as<double>(), g->nmat, g->eprops.as<double>());
+  } else {
+    if (g->id_bytes == 1)
+      edge_props_kernel<float, uint8_t><<<bl, MB, 0, s>>>(make_geo<float>(g), g->mat.as<uint8_t>(), g->mtab.as<float>(), g->nmat, g->eprops.as<float>());
+    else
+      edge_props_kernel<float, uint16_t><<<bl, MB, 0, s>>>(make_geo<float>(g), g->mat.as<uint16_t>(), g->mtab.as<float>(), g->nmat, g->eprops.as<float>());
+  }
+  FDTD_CHECK(after_launch("edge_props_kernel"));
+  g->eprops_ready = true;
+  return FDTD_OK;
+}
+
+// ------------------------------------------------------------------ operators
+template <typename T>
+struct OpArgs {
+  Geo<T> g;
+  const T *eps, *sig, *mu, *sgm;   // per-edge properties (3 x nc each)
+  T inv_dt;
+  cplx<T> z[kMaxRhs];              // expansion point of each right-hand side
+  cplx<T> cz[kMaxRhs];             // coefficient of the curl term
+};
+
+// r1 = (eps/dt + sig/2) v1, r2 = curlE(v1) + (mu/dt + sgm/2) v2   [(R+F) v]
+template <typename T>
+__global__ void rpf_kernel(OpArgs<T> a, const cplx<T> *__restrict__ v, int64_t vstride,
+                           cplx<T> *__restrict__ r, int64_t rstride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  const cplx<T> *vb = v + b * vstride;
+  cplx<T> *rb = r + b * rstride;
+  const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+  auto ld = [&](int64_t idx) { return vb[idx]; };
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const T ep = a.eps[e];
+    rb[e] = ep == T(0) ? cplx<T>() : (ep * a.inv_dt + T(0.5) * a.sig[e]) * vb[e];
+    const T mu = a.mu[e];
+    cplx<T> h;
+    if (mu != T(0)) h = curl_e_at<T, cplx<T>>(a.g, ld, c, i, j, k) + (mu * a.inv_dt + T(0.5) * a.sgm[e]) * vb[3 * nc + e];
+    rb[3 * nc + e] = h;
+  }
+}
+
+// t = (r2 + cz curlE(P x)) / a22(z); r2 and x optional; P optional diagonal.
+template <typename T>
+__global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int64_t xstride,
+                                const cplx<T> *__restrict__ P, int64_t pstride,
+                                const cplx<T> *__restrict__ r2, int64_t r2stride,
+                                cplx<T> *__restrict__ t, int64_t tstride, const int *__restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+  const cplx<T> *xb = x ? x + b * xstride : nullptr;
+  const cplx<T> *pb = P ? P + b * pstride : nullptr;
+  auto ld = [&](int64_t idx) { return pb ? pb[idx] * xb[idx] : xb[idx]; };
+  const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const T mu = a.mu[e];
+    cplx<T> out;
+    if (mu != T(0)) {
+      cplx<T> num;
+      if (r2) num = r2[b * r2stride + e];
+      if (xb) num = num + a.cz[b] * curl_e_at<T, cplx<T>>(a.g, ld, c, i, j, k);
+      const cplx<T> a22 = (mu * a.inv_dt) * zm1 + (T(0.5) * a.sgm[e]) * zp1;
+      out = cdiv(num, a22);
+    }
+    t[b * tstride + e] = out;
+  }
+}
+
+// Per right-hand-side scalars of the Krylov solvers (device resident).
+struct CgsScal {
+  double rho_re, rho_im, alpha_re, alpha_im, beta_re, beta_im, omega_re, omega_im, rn2, bn2;
+  int active, iters, status, restarts;
+};
+
+enum EMode { EM_RHS = 0, EM_APPLY = 1, EM_APPLY_DOT = 2, EM_APPLY_RUPDATE = 3, EM_RESID = 4 };
+enum ScalMode { SM_INIT = 0, SM_ALPHA = 1, SM_CGS_RHO = 2, SM_OMEGA = 3, SM_BICG_RHO = 4, SM_VERIFY = 5 };
+
+// Sums nv (<= 3) doubles over the block (blockDim.x a multiple of 32, <= 1024);
+// the totals are valid in vals[] of thread 0.  sh holds >= 3*32 doubles.
+__device__ __forceinline__ void block_sum(double *vals, int nv, double *sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = 0; q < nv; ++q) {
+    double v = vals[q];
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[q * 32 + w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nv; ++q) {
+      double acc = 0;
+      for (int ww = 0; ww < nw; ++ww) acc += sh[q * 32 + ww];
+      vals[q] = acc;
+    }
+  }
+}
+
+// y = A + cz curlH(t), A = r1 (EM_RHS) or a11(z) P x (apply modes); dead E edges 0.
+// EM_APPLY_DOT: partials of rt^H y and |y|^2.  EM_APPLY_RUPDATE: r -= alpha y,
+// partials of rt^H r and |r|^2 (y not stored).  EM_RESID: true residual
+// y = bhat - S x (bhat passed in rt), partials of |y|^2.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T> *__restrict__ t, int64_t tstride,
+                                const cplx<T> *__restrict__ x, int64_t xstride,
+                                const cplx<T> *__restrict__ P, int64_t pstride,
+                                cplx<T> *__restrict__ y, int64_t ystride,
+                                const cplx<T> *__restrict__ rt, cplx<T> *__restrict__ r, int64_t rstride,
+                                const CgsScal *__restrict__ sc, double *__restrict__ partials) {
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.y;
+  if (sc && MODE != EM_RESID && !sc[b].active) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  double acc[3] = {0, 0, 0};
+  if (n < nc) {
+    const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+    const cplx<T> *tb = t + b * tstride;
+    auto ld = [&](int64_t idx) { return tb[idx]; };
+    const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+    cplx<T> alpha;
+    if (MODE == EM_APPLY_RUPDATE) alpha = cplx<T>((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+    for (int c = 0; c < 3; ++c) {
+      const int64_t e = c * nc + n;
+      const T ep = a.eps[e];
+      cplx<T> out;
+      if (ep != T(0)) {
+        cplx<T> A;
+        if (MODE == EM_RHS) {
+          A = x[b * xstride + e];
+        } else {
+          const cplx<T> a11 = (ep * a.inv_dt) * zm1 + (T(0.5) * a.sig[e]) * zp1;
+          const cplx<T> px = P ? P[b * pstride + e] * x[b * xstride + e] : x[b * xstride + e];
+          A = a11 * px;
+        }
+        out = A + a.cz[b] * curl_h_at<T, cplx<T>>(a.g, ld, c, i, j, k);
+      }
+      if (MODE == EM_APPLY_DOT) {
+        const cplx<T> w = conj(rt[b * rstride + e]) * out;
+        acc[0] += (double)w.re;
+        acc[1] += (double)w.im;
+        acc[2] += (double)norm2(out);
+        y[b * ystride + e] = out;
+      } else if (MODE == EM_RESID) {
+        cplx<T> rv = rt[b * rstride + e] - out;
+        if (ep == T(0)) rv = cplx<T>();
+        y[b * ystride + e] = rv;
+        acc[0] += (double)norm2(rv);
+        acc[2] += (double)norm2(rv);
+      } else if (MODE == EM_APPLY_RUPDATE) {
+        cplx<T> rv = r[b * rstride + e] - alpha * out;
+        if (ep == T(0)) rv = cplx<T>();
+        r[b * rstride + e] = rv;
+        const cplx<T> w = conj(rt[b * rstride + e]) * rv;
+        acc[0] += (double)w.re;
+        acc[1] += (double)w.im;
+        acc[2] += (double)norm2(rv);
+      } else {
+        y[b * ystride + e] = out;
+      }
+    }
+  }
+  if (MODE == EM_APPLY_DOT || MODE == EM_APPLY_RUPDATE || MODE == EM_RESID) {
+    block_sum(acc, 3, sh);
+    if (threadIdx.x == 0) {
+      double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+      pb[0] = acc[0]; pb[1] = acc[1]; pb[2] = acc[2];
+    }
+  }
+}
+
+// Jacobi preconditioner: P = 1 / diag(S(z)) on live E edges, 0 on dead ones.
+template <typename T>
+__global__ void jacobi_kernel(OpArgs<T> a, cplx<T> *__restrict__ P, int64_t pstride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  const int nx = a.g.nx, ny = a.g.ny;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((int64_t)nx * ny));
+  const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+  auto inv_a22 = [&](int c, int ii, int jj, int kk) {
+    const int64_t e = c * nc + a.g.id(ii, jj, kk);
+    const cplx<T> a22 = (a.mu[e] * a.inv_dt) * zm1 + (T(0.5) * a.sgm[e]) * zp1;
+    return cdiv(cplx<T>(T(1)), a22);
+  };
+  const int idx[3] = {i, j, k};
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const T ep = a.eps[e];
+    cplx<T> out;
+    if (ep != T(0)) {
+      // transverse axes and the H component paired with each in curl H
+      const int ta[2] = {(c + 1) % 3, (c + 2) % 3};
+      const int hc[2] = {(c + 2) % 3, (c + 1) % 3};
+      cplx<T> sum;
+      for (int q = 0; q < 2; ++q) {
+        const int ax = ta[q], h = hc[q], ia = idx[ax];
+        int lo[3] = {i, j, k};
+        lo[ax] -= 1;
+        const cplx<T> t0 = inv_a22(h, i, j, k);
+        const cplx<T> t1 = inv_a22(h, lo[0], lo[1], lo[2]);
+        sum = sum + a.g.rdd(ax, ia) * (a.g.rd(ax, ia) * t0 + a.g.rd(ax, ia - 1) * t1);
+      }
+      const cplx<T> a11 = (ep * a.inv_dt) * zm1 + (T(0.5) * a.sig[e]) * zp1;
+      out = cdiv(cplx<T>(T(1)), a11 + a.z[b] * sum);
+    }
+    P[b * pstride + e] = out;
+  }
+}
+
+// CGS vector update 1: u = r + beta q; p = u + beta (q + beta p)
+template <typename T>
+__global__ void cgs_update1_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ r,
+                                   cplx<T> *__restrict__ q, cplx<T> *__restrict__ p, cplx<T> *__restrict__ u,
+                                   int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> beta((T)sc[b].beta_re, (T)sc[b].beta_im);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    const cplx<T> qq = q[o];
+    const cplx<T> uu = r[o] + beta * qq;
+    u[o] = uu;
+    p[o] = uu + beta * (qq + beta * p[o]);
+  }
+}
+
+// CGS vector update 2: q = u - alpha v; w = u + q; x += alpha P w  (w stored in v)
+template <typename T>
+__global__ void cgs_update2_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ u,
+                                   cplx<T> *__restrict__ v, cplx<T> *__restrict__ q, cplx<T> *__restrict__ x,
+                                   const cplx<T> *__restrict__ P, int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> alpha((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    const cplx<T> uu = u[o];
+    const cplx<T> qq = uu - alpha * v[o];
+    q[o] = qq;
+    const cplx<T> w = uu + qq;
+    v[o] = w;
+    x[o] = x[o] + alpha * (P[o] * w);
+  }
+}
+
+// Solver scalars from block partials (acc[0] + j acc[1] and acc[2] per RHS).
+//   SM_INIT:     rho = rt^H r = |r|^2, |b|^2 = |r|^2, beta = 0
+//   SM_ALPHA:    alpha = rho / (rt^H v)
+//   SM_CGS_RHO:  rho' = rt^H r, |r|^2 -> convergence; beta = rho'/rho      (CGS)
+//   SM_OMEGA:    omega = (t^H s)/(t^H t) from s^H t and |t|^2              (BiCGSTAB)
+//   SM_BICG_RHO: rho' = rt^H r, |r|^2 -> convergence; beta = (rho'/rho)(alpha/omega)
+//   SM_VERIFY:   true residual |b - S x|^2: restart (rt = r) when above tolerance
+__global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict__ partials, CgsScal *sc,
+                                      int mode, double tol, int maxit, int max_restarts) {
+  __shared__ double sh[3 * 32];
+  for (int b = 0; b < nb; ++b) {
+    if (mode != SM_VERIFY && mode != SM_INIT && !sc[b].active) continue;  // uniform across the block
+    if (mode == SM_VERIFY && sc[b].status == 1) continue;                  // iteration cap reached
+    double acc[3] = {0, 0, 0};
+    for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
+      const double *p = partials + ((size_t)b * nblk + blk) * 3;
+      acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
+    }
+    block_sum(acc, 3, sh);
+    if (threadIdx.x == 0) {
+      CgsScal &s = sc[b];
+      const cplx<double> rho(s.rho_re, s.rho_im), d(acc[0], acc[1]);
+      auto breakdown = [&]() { s.status = 2; s.active = 0; };
+      if (mode == SM_INIT) {
+        s.rho_re = acc[0]; s.rho_im = 0; s.rn2 = acc[2]; s.bn2 = acc[2];
+        s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
+        s.iters = 0; s.status = 0; s.restarts = 0;
+        s.active = acc[2] > 0 ? 1 : 0;   // zero right-hand side: x = 0
+      } else if (mode == SM_ALPHA) {
+        const double ad = sqrt(norm2(d));
+        if (ad == 0 || !isfinite(ad)) breakdown();
+        else { const cplx<double> al = cdiv(rho, d); s.alpha_re = al.re; s.alpha_im = al.im; }
+      } else if (mode == SM_OMEGA) {
+        if (!(acc[2] > 0) || !isfinite(acc[2])) breakdown();
+        else { s.omega_re = acc[0] / acc[2]; s.omega_im = -acc[1] / acc[2]; }
+        if (s.omega_re == 0 && s.omega_im == 0) breakdown();
+      } else if (mode == SM_CGS_RHO || mode == SM_BICG_RHO) {
+        s.rn2 = acc[2];
+        s.iters += 1;
+        if (!isfinite(acc[2])) breakdown();
+        else if (sqrt(acc[2]) <= tol * sqrt(s.bn2)) s.active = 0;
+        else if (s.iters >= maxit) { s.status = 1; s.active = 0; }
+        else if (norm2(rho) == 0) breakdown();
+        else {
+          cplx<double> be = cdiv(d, rho);
+          if (mode == SM_BICG_RHO) be = be * cdiv(cplx<double>(s.alpha_re, s.alpha_im), cplx<double>(s.omega_re, s.omega_im));
+          s.beta_re = be.re; s.beta_im = be.im;
+          s.rho_re = d.re; s.rho_im = d.im;
+        }
+      } else {  // SM_VERIFY: acc[2] = |b - S x|^2
+        s.rn2 = acc[2];
+        const bool ok = isfinite(acc[2]) && sqrt(acc[2]) <= 2.0 * tol * sqrt(s.bn2);
+        if (!ok && s.restarts < max_restarts && s.iters < maxit) {
+          s.restarts += 1; s.active = 1; s.status = 0;
+          s.rho_re = acc[2]; s.rho_im = 0; s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
+        } else if (!ok && s.status == 0) {
+          s.status = 3;  // true residual above tolerance after the last restart
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Restart of the active right-hand sides: shadow residual rt = r, search
+// directions zero.
+template <typename T>
+__global__ void solver_restart_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ r,
+                                      cplx<T> *__restrict__ rt, cplx<T> *__restrict__ p, cplx<T> *__restrict__ q,
+                                      int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    rt[o] = r[o];
+    p[o] = cplx<T>();
+    q[o] = cplx<T>();
+  }
+}
+
+// BiCGSTAB: p = r + beta (p - omega v)
+template <typename T>
+__global__ void bicg_update_p_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ r,
+                                     const cplx<T> *__restrict__ v, cplx<T> *__restrict__ p, int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> beta((T)sc[b].beta_re, (T)sc[b].beta_im), om((T)sc[b].omega_re, (T)sc[b].omega_im);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    p[o] = r[o] + beta * (p[o] - om * v[o]);
+  }
+}
+
+// BiCGSTAB: s = r - alpha v
+template <typename T>
+__global__ void bicg_update_s_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ r,
+                                     const cplx<T> *__restrict__ v, cplx<T> *__restrict__ sv, int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> al((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    sv[o] = r[o] - al * v[o];
+  }
+}
+
+// BiCGSTAB: x += alpha P p + omega P s; r = s - omega t; partials rt^H r, |r|^2
+template <typename T>
+__global__ void __launch_bounds__(MB) bicg_update_xr_kernel(int64_t len, const CgsScal *__restrict__ sc,
+                                      const cplx<T> *__restrict__ P, const cplx<T> *__restrict__ p,
+                                      const cplx<T> *__restrict__ sv, const cplx<T> *__restrict__ tv,
+                                      const cplx<T> *__restrict__ rt, cplx<T> *__restrict__ x, cplx<T> *__restrict__ r,
+                                      int64_t stride, double *__restrict__ partials) {
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> al((T)sc[b].alpha_re, (T)sc[b].alpha_im), om((T)sc[b].omega_re, (T)sc[b].omega_im);
+  double acc[3] = {0, 0, 0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    const cplx<T> pw = P[o];
+    x[o] = x[o] + pw * (al * p[o] + om * sv[o]);
+    const cplx<T> rv = sv[o] - om * tv[o];
+    r[o] = rv;
+    const cplx<T> w = conj(rt[o]) * rv;
+    acc[0] += (double)w.re; acc[1] += (double)w.im; acc[2] += (double)norm2(rv);
+  }
+  block_sum(acc, 3, sh);
+  if (threadIdx.x == 0) {
+    double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+    pb[0] = acc[0]; pb[1] = acc[1]; pb[2] = acc[2];
+  }
+}
+
+// partials for the init: rt = r (copy), rho = r^H r, |r|^2
+template <typename T>
+__global__ void __launch_bounds__(MB) cgs_init_kernel(int64_t len, const cplx<T> *__restrict__ bhat, cplx<T> *__restrict__ r,
+                                cplx<T> *__restrict__ rt, cplx<T> *__restrict__ x, cplx<T> *__restrict__ p,
+                                cplx<T> *__restrict__ q, int64_t stride, double *__restrict__ partials) {
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.y;
+  double acc[3] = {0, 0, 0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    const cplx<T> v = bhat[o];
+    r[o] = v; rt[o] = v; x[o] = cplx<T>(); p[o] = cplx<T>(); q[o] = cplx<T>();
+    const double n2 = (double)norm2(v);
+    acc[0] += n2; acc[2] += n2;
+  }
+  block_sum(acc, 3, sh);
+  if (threadIdx.x == 0) {
+    double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+    pb[0] = acc[0]; pb[1] = 0; pb[2] = acc[2];
+  }
+}
+
+// ------------------------------------------------------- Gram-Schmidt pieces
+// partial dots h[c] = sum_i conj(Q[c][i]) x[i], c < nq (V: T or cplx<T>)
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) multidot_kernel(int64_t len, const V *__restrict__ Q, int64_t qstride, int nq,
+                                                       const V *__restrict__ x, double *__restrict__ partials) {
+  constexpr int CH = 8;  // elements per thread
+  __shared__ __align__(16) unsigned char xs_raw[256 * CH * sizeof(V)];
+  V *xs = reinterpret_cast<V *>(xs_raw);
+  __shared__ double wsum[kMaxDots * 2 * 8];
+  const int64_t base = (int64_t)blockIdx.x * 256 * CH;
+  for (int t = 0; t < CH; ++t) {
+    const int64_t e = base + t * 256 + threadIdx.x;
+    xs[t * 256 + threadIdx.x] = e < len ? x[e] : V(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < nq; ++c) {
+    double re = 0, im = 0;
+    const V *qc = Q + c * qstride;
+    for (int t = 0; t < CH; ++t) {
+      const int64_t e = base + t * 256 + threadIdx.x;
+      if (e < len) {
+        const V qv = qc[e], xv = xs[t * 256 + threadIdx.x];
+        if constexpr (sizeof(V) == 2 * sizeof(T)) {
+          const cplx<T> pr = conj(*(const cplx<T> *)&qv) * *(const cplx<T> *)&xv;
+          re += (double)pr.re; im += (double)pr.im;
+        } else {
+          re += (double)(*(const T *)&qv) * (double)(*(const T *)&xv);
+        }
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) { wsum[(c * 2) * 8 + w] = re; wsum[(c * 2 + 1) * 8 + w] = im; }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * nq; q += 256) {
+    double a = 0;
+    for (int ww = 0; ww < 8; ++ww) a += wsum[q * 8 + ww];
+    partials[(size_t)q * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// h[q] = sum over blocks of partials (2*nq values, complex as re/im pairs)
+__global__ void reduce_partials_kernel(int nvals, int nblk, const double *__restrict__ partials,
+                                       double *__restrict__ out) {
+  const int q = blockIdx.x;
+  if (q >= nvals) return;
+  double a = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += partials[(size_t)q * nblk + b];
+  for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    out[q] = t;
+  }
+}
+
+// x -= sum_c Q[c] h[c]
+template <typename T, typename V>
+__global__ void multiaxpy_kernel(int64_t len, const V *__restrict__ Q, int64_t qstride, int nq,
+                                 const double *__restrict__ h, V *__restrict__ x) {
+  __shared__ double hs[kMaxDots * 2];
+  for (int q = threadIdx.x; q < 2 * nq; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(V) == 2 * sizeof(T)) {
+      cplx<T> acc = *(const cplx<T> *)&x[e];
+      for (int c = 0; c < nq; ++c) {
+        const cplx<T> qv = *(const cplx<T> *)&Q[c * qstride + e];
+        acc = acc - cplx<T>((T)hs[2 * c], (T)hs[2 * c + 1]) * qv;
+      }
+      *(cplx<T> *)&x[e] = acc;
+    } else {
+      T acc = *(const T *)&x[e];
+      for (int c = 0; c < nq; ++c) acc -= (T)hs[2 * c] * *(const T *)&Q[c * qstride + e];
+      *(T *)&x[e] = acc;
+    }
+  }
+}
+
+// out = x * s (s = 1/norm from device), or plain copy when s == nullptr
+template <typename V, typename T>
+__global__ void scale_copy_kernel(int64_t len, const V *__restrict__ x, V *__restrict__ out, T s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(V) == 2 * sizeof(T)) {
+      const cplx<T> v = *(const cplx<T> *)&x[e];
+      *(cplx<T> *)&out[e] = s * v;
+    } else {
+      *(T *)&out[e] = s * *(const T *)&x[e];
+    }
+  }
+}
+
+// real part (part = 0) or imaginary part (part = 1) of a complex vector
+template <typename T>
+__global__ void take_part_kernel(int64_t len, const cplx<T> *__restrict__ x, int part, T *__restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = part ? x[e].im : x[e].re;
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+struct Work {
+  int nb = 0;
+  int64_t nc = 0;
+  DevBuf v;        // nb x 6nc complex: current chain vector (input to (R+F))
+  DevBuf r;        // nb x 6nc complex: (R+F) v
+  DevBuf bhat;     // nb x 3nc
+  DevBuf P;        // nb x 3nc preconditioner
+  DevBuf x, rr, rt, u, p, q, vv;   // nb x 3nc CGS vectors
+  DevBuf t;        // nb x 3nc H-part temporary
+  DevBuf partials; // nb x nblk x 3 doubles
+  DevBuf sc;       // nb CgsScal
+  DevBuf dots;     // kMaxDots*2 doubles
+  DevBuf dpart;    // 2*kMaxDots x nblk_dot doubles
+};
+
+template <typename T>
+static OpArgs<T> make_op(fdtd_grid *g, double dt0, const std::vector<std::complex<double>> &zs,
+                         const std::vector<std::complex<double>> &czs) {
+  OpArgs<T> a;
+  a.g = make_geo<T>(g);
+  const T *ep = g->eprops.as<T>();
+  a.eps = ep + EP_EPS * 3 * g->nc;
+  a.sig = ep + EP_SIG * 3 * g->nc;
+  a.mu = ep + EP_MU * 3 * g->nc;
+  a.sgm = ep + EP_SGM * 3 * g->nc;
+  a.inv_dt = (T)(1.0 / dt0);
+  for (size_t b = 0; b < zs.size(); ++b) {
+    a.z[b] = cplx<T>((T)zs[b].real(), (T)zs[b].imag());
+    a.cz[b] = cplx<T>((T)czs[b].real(), (T)czs[b].imag());
+  }
+  return a;
+}
+
+template <typename T>
+struct BasisBuilder {
+  fdtd_grid *g;
+  const mor_opts o;
+  cudaStream_t s;
+  int64_t nc;
+  int nblk;
+  int max_iters = 0;
+  double max_resid = 0;
+  bool noconv = false;
+
+  BasisBuilder(fdtd_grid *g_, const mor_opts &o_, cudaStream_t s_) : g(g_), o(o_), s(s_) {
+    nc = g->nc;
+    nblk = (int)((nc + MB - 1) / MB);
+  }
+
+  // Solve A(z_b) x = (R+F) v for every active right-hand side b (x = [x1; x2]
+  // written to out, nb x 6nc).  v: nb x 6nc.
+  fdtd_status solve(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
+                    const cplx<T> *vin, cplx<T> *out) {
+    const int nb = (int)zs.size();
+    const int64_t n3 = 3 * nc, n6 = 6 * nc;
+    std::vector<std::complex<double>> one(nb, 1.0), negz(nb), zz(zs);
+    for (int b = 0; b < nb; ++b) negz[b] = -zs[b];
+    dim3 grid2(nblk, nb);
+    cplx<T> *r = w.r.template as<cplx<T>>();
+    if (!from_b) {
+      OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
+      rpf_kernel<T><<<grid2, MB, 0, s>>>(a, vin, n6, r, n6);
+      FDTD_CHECK(after_launch("rpf_kernel"));
+    }
+    // b^ = r1 + curlH(r2 / a22)
+    cplx<T> *t = w.t.template as<cplx<T>>();
+    {
+      OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
+      h_from_e_kernel<T><<<grid2, MB, 0, s>>>(a, nullptr, 0, nullptr, 0, r + n3, n6, t, n3, nullptr);
+      FDTD_CHECK(after_launch("h_from_e_kernel"));
+      e_from_h_kernel<T, EM_RHS><<<grid2, MB, 0, s>>>(a, t, n3, r, n6, nullptr, 0, w.bhat.template as<cplx<T>>(), n3,
+                                                      nullptr, nullptr, 0, nullptr, nullptr);
+      FDTD_CHECK(after_launch("e_from_h_kernel"));
+    }
+    // S x = a11 x + z curlH(curlE(x)/a22): the curlE half carries no factor,
+    // the curlH half carries z.
+    OpArgs<T> ap = make_op<T>(g, o.dt0, zs, zz);       // e_from_h half: cz = z
+    OpArgs<T> ah1 = make_op<T>(g, o.dt0, zs, one);     // h_from_e half: cz = 1
+    CgsScal *sc = w.sc.template as<CgsScal>();
+    std::vector<CgsScal> hsc(nb);
+    for (auto &x : hsc) { x = CgsScal{}; x.active = 1; }
+    const bool trace = getenv("FDTDMOR_TRACE") != nullptr;
+    const int solver = o.solver == MOR_SOLVER_AUTO ? (g->prec == FDTD_F64 ? MOR_SOLVER_CGS : MOR_SOLVER_BICGSTAB)
+                                                   : o.solver;
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(sc, hsc.data(), sizeof(CgsScal) * nb, cudaMemcpyHostToDevice, s));
+    cplx<T> *P = w.P.template as<cplx<T>>(), *x = w.x.template as<cplx<T>>(), *rr = w.rr.template as<cplx<T>>();
+    cplx<T> *rt = w.rt.template as<cplx<T>>(), *u = w.u.template as<cplx<T>>(), *p = w.p.template as<cplx<T>>();
+    cplx<T> *q = w.q.template as<cplx<T>>(), *vv = w.vv.template as<cplx<T>>();
+    double *part = w.partials.template as<double>();
+    jacobi_kernel<T><<<grid2, MB, 0, s>>>(ap, P, n3);
+    FDTD_CHECK(after_launch("jacobi_kernel"));
+    const int eblk = std::min(nblk, 152 * 8);
+    dim3 gridE(eblk, nb);
+    cgs_init_kernel<T><<<gridE, MB, 0, s>>>(n3, w.bhat.template as<cplx<T>>(), rr, rt, x, p, q, n3, part);
+    FDTD_CHECK(after_launch("cgs_init_kernel"));
+    FDTD_CHECK_CUDA(cudaMemsetAsync(vv, 0, sizeof(cplx<T>) * nb * n3, s));
+    solver_scalars_kernel<<<1, 256, 0, s>>>(nb, eblk, part, sc, SM_INIT, o.tol, o.maxit, kMaxRestarts);
+    FDTD_CHECK(after_launch("solver_scalars_kernel"));
+    auto scal = [&](int mode, int nbk) -> fdtd_status {
+      solver_scalars_kernel<<<1, 256, 0, s>>>(nb, nbk, part, sc, mode, o.tol, o.maxit, kMaxRestarts);
+      return after_launch("solver_scalars_kernel");
+    };
+    const bool bicg = solver == MOR_SOLVER_BICGSTAB;
+    cplx<T> *bh_ = w.bhat.template as<cplx<T>>();
+    const int poll = 16;
+    int it = 0;
+    for (int round = 0; round <= kMaxRestarts; ++round) {
+      for (; it < o.maxit + poll; ++it) {
+        if (!bicg) {
+          // conjugate gradient squared (right-preconditioned, P = Jacobi)
+          // u = r + beta q; p = u + beta (q + beta p)
+          cgs_update1_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, q, p, u, n3);
+          FDTD_CHECK(after_launch("cgs_update1_kernel"));
+          // v = S P p, sigma = rt^H v
+          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
+          FDTD_CHECK(after_launch("h_from_e_kernel"));
+          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
+          FDTD_CHECK(after_launch("e_from_h_kernel"));
+          FDTD_CHECK(scal(SM_ALPHA, nblk));
+          // q = u - alpha v; w = u + q (into vv); x += alpha P w
+          cgs_update2_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, u, vv, q, x, P, n3);
+          FDTD_CHECK(after_launch("cgs_update2_kernel"));
+          // r -= alpha S P w; rho = rt^H r; |r|^2
+          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, vv, n3, P, n3, nullptr, 0, t, n3, nullptr);
+          FDTD_CHECK(after_launch("h_from_e_kernel"));
+          e_from_h_kernel<T, EM_APPLY_RUPDATE><<<grid2, MB, 0, s>>>(ap, t, n3, vv, n3, P, n3, nullptr, 0, rt, rr, n3, sc, part);
+          FDTD_CHECK(after_launch("e_from_h_kernel"));
+          FDTD_CHECK(scal(SM_CGS_RHO, nblk));
+        } else {
+          // BiCGSTAB (right-preconditioned, P = Jacobi); p in p, v in vv, s in u, t in q
+          bicg_update_p_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, vv, p, n3);
+          FDTD_CHECK(after_launch("bicg_update_p_kernel"));
+          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
+          FDTD_CHECK(after_launch("h_from_e_kernel"));
+          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
+          FDTD_CHECK(after_launch("e_from_h_kernel"));
+          FDTD_CHECK(scal(SM_ALPHA, nblk));
+          bicg_update_s_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, vv, u, n3);
+          FDTD_CHECK(after_launch("bicg_update_s_kernel"));
+          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, u, n3, P, n3, nullptr, 0, t, n3, nullptr);
+          FDTD_CHECK(after_launch("h_from_e_kernel"));
+          // t = S P s with partials s^H t and |t|^2
+          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, u, n3, P, n3, q, n3, u, nullptr, n3, sc, part);
+          FDTD_CHECK(after_launch("e_from_h_kernel"));
+          FDTD_CHECK(scal(SM_OMEGA, nblk));
+          bicg_update_xr_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, P, p, u, q, rt, x, rr, n3, part);
+          FDTD_CHECK(after_launch("bicg_update_xr_kernel"));
+          FDTD_CHECK(scal(SM_BICG_RHO, eblk));
+        }
+        if ((it + 1) % poll == 0) {
+          FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+          FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+          bool any = false;
+          for (auto &x2 : hsc) any |= x2.active != 0;
+          if (trace) {
+            fprintf(stderr, "[%s] it %d", bicg ? "bicgstab" : "cgs", it + 1);
+            for (auto &x2 : hsc) fprintf(stderr, " %.3e%s", x2.bn2 > 0 ? std::sqrt(x2.rn2 / x2.bn2) : 0.0, x2.active ? "" : "*");
+            fprintf(stderr, "\n");
+          }
+          if (!any) { ++it; break; }
+        }
+      }
+      // verify with the true residual b - S x; restart the ones above tolerance
+      h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, x, n3, nullptr, 0, nullptr, 0, t, n3, nullptr);
+      FDTD_CHECK(after_launch("h_from_e_kernel"));
+      e_from_h_kernel<T, EM_RESID><<<grid2, MB, 0, s>>>(ap, t, n3, x, n3, nullptr, 0, rr, n3, bh_, nullptr, n3, sc, part);
+      FDTD_CHECK(after_launch("e_from_h_kernel"));
+      FDTD_CHECK(scal(SM_VERIFY, nblk));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+      bool any = false;
+      for (auto &x2 : hsc) any |= x2.active != 0;
+      if (trace) {
+        fprintf(stderr, "[verify] round %d true residual", round);
+        for (auto &x2 : hsc) fprintf(stderr, " %.3e%s", x2.bn2 > 0 ? std::sqrt(x2.rn2 / x2.bn2) : 0.0, x2.active ? " (restart)" : "");
+        fprintf(stderr, "\n");
+      }
+      if (!any) break;
+      solver_restart_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, rt, p, q, n3);
+      FDTD_CHECK(after_launch("solver_restart_kernel"));
+      if (bicg) FDTD_CHECK_CUDA(cudaMemsetAsync(vv, 0, sizeof(cplx<T>) * nb * n3, s));
+    }
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (auto &x2 : hsc) {
+      max_iters = std::max(max_iters, x2.iters);
+      if (x2.bn2 > 0) max_resid = std::max(max_resid, std::sqrt(x2.rn2 / x2.bn2));
+      if (x2.status != 0 || x2.active) noconv = true;
+    }
+    // out = [x1; x2], x2 = (r2 - z curlE(x1)) / a22
+    for (int b = 0; b < nb; ++b) {
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(out + b * n6, x + b * n3, sizeof(cplx<T>) * n3, cudaMemcpyDeviceToDevice, s));
+    }
+    OpArgs<T> ah = make_op<T>(g, o.dt0, zs, negz);
+    // h_from_e writes its output with stride tstride; point it at the H half of out
+    h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah, x, n3, nullptr, 0, r + n3, n6, out + n3, n6, nullptr);
+    FDTD_CHECK(after_launch("h_from_e_kernel"));
+    return FDTD_OK;
+  }
+
+  // Gram-Schmidt of vec (len) against Q[0..nq) (stride qstride), two passes,
+  // returns the norm before (n0) and after (n1) via host sync.
+  template <typename V>
+  fdtd_status cgs2(Work<T> &w, const V *Q, int64_t qstride, int nq, V *vec, int64_t len, double &n0,
+                   double &n1) {
+    const int dblk = (int)((len + 256 * 8 - 1) / (256 * 8));
+    FDTD_CHECK(w.dpart.alloc(sizeof(double) * 2 * (kMaxDots + 1) * dblk, s));
+    double *dp = w.dpart.template as<double>();
+    double *h = w.dots.template as<double>();
+    auto norm = [&](double &out) -> fdtd_status {
+      multidot_kernel<T, V><<<dblk, 256, 0, s>>>(len, vec, 0, 1, vec, dp);
+      FDTD_CHECK(after_launch("multidot_kernel"));
+      reduce_partials_kernel<<<2, 256, 0, s>>>(2, dblk, dp, h);
+      FDTD_CHECK(after_launch("reduce_partials_kernel"));
+      double hh[2];
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(hh, h, sizeof(hh), cudaMemcpyDeviceToHost, s));
+      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+      out = std::sqrt(std::max(hh[0], 0.0));
+      return FDTD_OK;
+    };
+    FDTD_CHECK(norm(n0));
+    for (int pass = 0; pass < 2 && nq > 0; ++pass) {
+      for (int c0 = 0; c0 < nq; c0 += kMaxDots) {
+        const int cn = std::min(kMaxDots, nq - c0);
+        multidot_kernel<T, V><<<dblk, 256, 0, s>>>(len, Q + c0 * qstride, qstride, cn, vec, dp);
+        FDTD_CHECK(after_launch("multidot_kernel"));
+        reduce_partials_kernel<<<2 * cn, 256, 0, s>>>(2 * cn, dblk, dp, h);
+        FDTD_CHECK(after_launch("reduce_partials_kernel"));
+        multiaxpy_kernel<T, V><<<std::min<int64_t>((len + 255) / 256, 152 * 16), 256, 0, s>>>(len, Q + c0 * qstride, qstride, cn, h, vec);
+        FDTD_CHECK(after_launch("multiaxpy_kernel"));
+      }
+    }
+    FDTD_CHECK(norm(n1));
+    return FDTD_OK;
+  }
+};
+
+
+template <typename T>
+static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s, mor_basis *B) {
+  FDTD_CHECK(ensure_edge_props(g, s));
+  const int m = (int)g->ports.size();
+  FDTD_REQUIRE(m >= 1, "mor_build_basis: the grid has no sources (B has no columns)");
+  // expansion points, l = 0..L (conjugates implied)
+  std::vector<std::complex<double>> pts;
+  if (o.include_center) {
+    for (int l = 0; l <= o.L; ++l) {
+      const double ang = 2 * kPi * (o.L ? (double)l / o.L : 0.0) * o.fmax * o.dt0;
+      pts.push_back(l == 0 ? std::complex<double>(o.M, 0) : std::polar(o.M, ang));
+    }
+  } else {
+    pts.push_back(std::polar(o.M, 2 * kPi * o.fmax * o.dt0));
+  }
+  int nreal = 0;
+  for (auto &z : pts) nreal += (z.imag() == 0.0) ? 1 : 2;
+  const int k = std::max(1, o.q / (nreal * m));
+  const int np = (int)pts.size();
+  const int nb = np * m;
+  FDTD_REQUIRE(nb <= kMaxRhs, "too many expansion points x ports (max %d)", kMaxRhs);
+  FDTD_REQUIRE(k * m <= kMaxDots * 64, "chain too long");
+  const int64_t nc = g->nc, n3 = 3 * nc, n6 = 6 * nc;
+  BasisBuilder<T> bb(g, o, s);
+  Work<T> w;
+  w.nb = nb;
+  const size_t cb = sizeof(cplx<T>);
+  FDTD_CHECK(w.v.alloc(cb * nb * n6, s));
+  FDTD_CHECK(w.r.alloc(cb * nb * n6, s));
+  for (DevBuf *d : {&w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t}) FDTD_CHECK(d->alloc(cb * nb * n3, s));
+  FDTD_CHECK(w.partials.alloc(sizeof(double) * 3 * nb * (size_t)bb.nblk, s));
+  FDTD_CHECK(w.sc.alloc(sizeof(CgsScal) * nb, s));
+  FDTD_CHECK(w.dots.alloc(sizeof(double) * 2 * (kMaxDots + 1), s));
+  // chains: per point, k*m complex vectors of 6nc
+  const int clen = k * m;
+  DevBuf chains;
+  FDTD_CHECK(chains.alloc(cb * (size_t)np * clen * n6, s));
+  cplx<T> *Qc = chains.as<cplx<T>>();
+  std::vector<int> ccount(np, 0);
+  DevBuf xs;
+  FDTD_CHECK(xs.alloc(cb * nb * n6, s));
+  cplx<T> *X = xs.as<cplx<T>>();
+  std::vector<std::complex<double>> zs(nb);
+  for (int pidx = 0; pidx < np; ++pidx)
+    for (int c = 0; c < m; ++c) zs[pidx * m + c] = pts[pidx];
+  // v_0 = A^{-1} B: right-hand side (R+F)-free, r = [B_E column / V_e; 0]
+  {
+    // B column in the per-volume form: -w at the source edges
+    std::vector<cplx<T>> host((size_t)nb * n6);
+    for (int b = 0; b < nb; ++b) {
+      const HostPort &hp = g->ports[b % m];
+      for (size_t e = 0; e < hp.cell.size(); ++e) {
+        cplx<T> &dst = host[(size_t)b * n6 + (size_t)hp.comp * nc + hp.cell[e]];
+        dst = dst + cplx<T>((T)(-hp.w[e]));
+      }
+    }
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(w.r.ptr, host.data(), cb * host.size(), cudaMemcpyHostToDevice, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  // dead source edges (PEC) must carry no right-hand side: r1 is masked by
+  // e_from_h (A = r1 only on live edges), so nothing else to do here.
+  for (int j = 0; j < k; ++j) {
+    FDTD_CHECK(bb.solve(w, zs, j == 0, w.v.template as<cplx<T>>(), X));
+    // block Arnoldi per point: each new column against the whole chain
+    for (int c = 0; c < m; ++c) {
+      for (int pidx = 0; pidx < np; ++pidx) {
+        const int b = pidx * m + c;
+        cplx<T> *vec = X + (size_t)b * n6;
+        cplx<T> *chain = Qc + (size_t)pidx * clen * n6;
+        double n0, n1;
+        FDTD_CHECK(bb.cgs2(w, chain, n6, ccount[pidx], vec, n6, n0, n1));
+        cplx<T> *dst = chain + (size_t)ccount[pidx] * n6;
+        if (n1 > 0 && std::isfinite(n1)) {
+          scale_copy_kernel<cplx<T>, T><<<std::min<int64_t>((n6 + 255) / 256, 152 * 16), 256, 0, s>>>(n6, vec, dst, (T)(1.0 / n1));
+          FDTD_CHECK(after_launch("scale_copy_kernel"));
+          // next moment starts from the orthonormal vector
+          FDTD_CHECK_CUDA(cudaMemcpyAsync(w.v.template as<cplx<T>>() + (size_t)b * n6, dst, cb * n6, cudaMemcpyDeviceToDevice, s));
+          ccount[pidx] += 1;
+        } else {
+          FDTD_CHECK_CUDA(cudaMemcpyAsync(w.v.template as<cplx<T>>() + (size_t)b * n6, vec, cb * n6, cudaMemcpyDeviceToDevice, s));
+        }
+      }
+    }
+  }
+  // SPRIM split + CGS2 with deflation, pool order: point, chain order, Re then Im
+  std::vector<std::pair<int, int>> pool;  // (point, chain index)
+  int qmax = 0;
+  for (int pidx = 0; pidx < np; ++pidx) {
+    const int parts = pts[pidx].imag() == 0.0 ? 1 : 2;
+    qmax += parts * ccount[pidx];
+  }
+  FDTD_CHECK(B->V1.alloc(sizeof(T) * std::max(1, qmax) * n3, s));
+  FDTD_CHECK(B->V2.alloc(sizeof(T) * std::max(1, qmax) * n3, s));
+  DevBuf tmp;
+  FDTD_CHECK(tmp.alloc(sizeof(T) * n3, s));
+  T *wv = tmp.as<T>();
+  for (int half = 0; half < 2; ++half) {
+    T *V = (half == 0 ? B->V1 : B->V2).as<T>();
+    int qc = 0;
+    for (int pidx = 0; pidx < np; ++pidx) {
+      const int parts = pts[pidx].imag() == 0.0 ? 1 : 2;
+      for (int c = 0; c < ccount[pidx]; ++c) {
+        for (int part = 0; part < parts; ++part) {
+          const cplx<T> *src = Qc + ((size_t)pidx * clen + c) * n6 + (half ? n3 : 0);
+          take_part_kernel<T><<<std::min<int64_t>((n3 + 255) / 256, 152 * 16), 256, 0, s>>>(n3, src, part, wv);
+          FDTD_CHECK(after_launch("take_part_kernel"));
+          double n0, n1;
+          FDTD_CHECK(bb.cgs2(w, V, n3, qc, wv, n3, n0, n1));
+          if (n0 > 0 && n1 >= o.defl_tol * n0) {
+            scale_copy_kernel<T, T><<<std::min<int64_t>((n3 + 255) / 256, 152 * 16), 256, 0, s>>>(n3, wv, V + (size_t)qc * n3, (T)(1.0 / n1));
+            FDTD_CHECK(after_launch("scale_copy_kernel"));
+            ++qc;
+          }
+        }
+      }
+    }
+    (half == 0 ? B->q1 : B->q2) = qc;
+  }
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  for (DevBuf *d : {&w.v, &w.r, &w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc, &w.dots, &w.dpart, &chains, &xs, &tmp})
+    d->release(s);
+  B->max_iters = bb.max_iters;
+  B->max_resid = bb.max_resid;
+  return bb.noconv ? FDTD_ENOCONV : FDTD_OK;
+}
+
+}  // namespace fdtdmor
+
+using namespace fdtdmor;
+
+extern "C" {
+
+fdtd_status mor_opts_default(mor_opts *o) {
+  FDTD_REQUIRE(o, "mor_opts_default: NULL");
+  o->q = 0; o->L = 2; o->M = 1.1; o->fmax = 0; o->dt0 = 0; o->include_center = 1;
+  o->tol = 1e-4; o->maxit = 20000; o->defl_tol = 1e-8; o->orth = MOR_ORTH_NATIVE;
+  o->solver = MOR_SOLVER_AUTO;
+  return FDTD_OK;
+}
+
+fdtd_status mor_build_basis(fdtd_grid *g, const mor_opts *o, fdtd_stream_t stream, mor_basis **out) {
+  FDTD_REQUIRE(g && o && out, "mor_build_basis: NULL argument");
+  *out = nullptr;
+  FDTD_REQUIRE(o->q >= 1 && o->L >= 0 && o->M > 0 && o->dt0 > 0 && o->tol > 0 && o->maxit >= 1,
+               "mor_build_basis: need q >= 1, L >= 0, M > 0, dt0 > 0, tol > 0, maxit >= 1");
+  FDTD_REQUIRE(o->defl_tol >= 0 && o->defl_tol < 1, "defl_tol must be in [0, 1)");
+  FDTD_REQUIRE(o->include_center || o->fmax > 0, "the pair of points needs fmax > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  mor_basis *B = new mor_basis();
+  B->n3 = 3 * g->nc;
+  B->elem = g->elem;
+  B->prec = g->prec;
+  B->stream = s;
+  fdtd_status st = g->prec == FDTD_F64 ? build_basis_t<double>(g, *o, s, B) : build_basis_t<float>(g, *o, s, B);
+  if (st != FDTD_OK && st != FDTD_ENOCONV) {
+    mor_basis_destroy(B);
+    return st;
+  }
+  *out = B;
+  if (st == FDTD_ENOCONV) set_error("a shifted solve reached maxit (worst relative residual %.3e)", B->max_resid);
+  return st;
+}
+
+fdtd_status mor_basis_info(const mor_basis *b, int *q1, int *q2, int *max_iters, double *max_resid) {
+  FDTD_REQUIRE(b, "mor_basis_info: NULL basis");
+  if (q1) *q1 = b->q1;
+  if (q2) *q2 = b->q2;
+  if (max_iters) *max_iters = b->max_iters;
+  if (max_resid) *max_resid = b->max_resid;
+  return FDTD_OK;
+}
+
+fdtd_status mor_basis_get(const mor_basis *b, int which, void *dst, fdtd_stream_t stream) {
+  FDTD_REQUIRE(b && dst && (which == 1 || which == 2), "mor_basis_get: bad argument");
+  const int q = which == 1 ? b->q1 : b->q2;
+  const DevBuf &src = which == 1 ? b->V1 : b->V2;
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(dst, src.ptr, (size_t)q * b->n3 * b->elem, cudaMemcpyDefault, (cudaStream_t)stream));
+  return FDTD_OK;
+}
+
+fdtd_status fdtd_edge_props_get(fdtd_grid *g, void *dst, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g && dst, "fdtd_edge_props_get: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  FDTD_CHECK(ensure_edge_props(g, s));
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(dst, g->eprops.ptr, (size_t)12 * g->nc * g->elem, cudaMemcpyDefault, s));
+  return FDTD_OK;
+}
+
+fdtd_status mor_basis_destroy(mor_basis *b) {
+  if (!b) return FDTD_OK;
+  cudaStreamSynchronize(b->stream);
+  b->V1.release(b->stream);
+  b->V2.release(b->stream);
+  cudaStreamSynchronize(b->stream);
+  delete b;
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Device helpers shared by the reduction kernels: complex arithmetic, the two
+// discrete curls of Eq. (matrix) in the per-volume form, per-edge material
+// properties and the reduction handles.
+#pragma once
+
+#include "common.cuh"
+
+namespace fdtdmor {
+
+template <typename T>
+struct cplx {
+  T re, im;
+  __host__ __device__ cplx() : re(0), im(0) {}
+  __host__ __device__ cplx(T r, T i = T(0)) : re(r), im(i) {}
+};
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> conj(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T> __host__ __device__ __forceinline__ T norm2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cdiv(cplx<T> a, cplx<T> b) {
+  T d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+template <typename T, typename U> __host__ __device__ __forceinline__ cplx<T> ccast(cplx<U> a) { return {(T)a.re, (T)a.im}; }
+
+// Geometry view for stencils over the storage layout.
+template <typename T>
+struct Geo {
+  int nx, ny, nz;
+  int64_t nc;
+  const T *ax;  // axis tables
+  __device__ __forceinline__ int ntot() const { return nx + ny + nz; }
+  __device__ __forceinline__ T rd(int axis, int i) const { return __ldg(ax + AX_RD * ntot() + off(axis) + i); }
+  __device__ __forceinline__ T rdd(int axis, int i) const { return __ldg(ax + AX_RDD * ntot() + off(axis) + i); }
+  __device__ __forceinline__ int off(int axis) const { return axis == 0 ? 0 : (axis == 1 ? nx : nx + ny); }
+  __device__ __forceinline__ int64_t id(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
+};
+
+// (curl E)_c at H edge (i, j, k) of a 3-component vector field x (stride nc),
+// values outside the box are zero (tangential E on the PEC walls).
+template <typename T, typename V, typename LD>
+__device__ __forceinline__ V curl_e_at(const Geo<T> &g, LD ld, int c, int i, int j, int k) {
+  const int64_t n = g.id(i, j, k), nc = g.nc;
+  V z(0);
+  if (c == 0) {
+    V ezp = (j + 1 < g.ny) ? ld(2 * nc + g.id(i, j + 1, k)) : z;
+    V eyp = (k + 1 < g.nz) ? ld(1 * nc + g.id(i, j, k + 1)) : z;
+    return g.rd(1, j) * (ezp - ld(2 * nc + n)) - g.rd(2, k) * (eyp - ld(1 * nc + n));
+  } else if (c == 1) {
+    V exp_ = (k + 1 < g.nz) ? ld(0 * nc + g.id(i, j, k + 1)) : z;
+    V ezp = (i + 1 < g.nx) ? ld(2 * nc + g.id(i + 1, j, k)) : z;
+    return g.rd(2, k) * (exp_ - ld(0 * nc + n)) - g.rd(0, i) * (ezp - ld(2 * nc + n));
+  } else {
+    V eyp = (i + 1 < g.nx) ? ld(1 * nc + g.id(i + 1, j, k)) : z;
+    V exp_ = (j + 1 < g.ny) ? ld(0 * nc + g.id(i, j + 1, k)) : z;
+    return g.rd(0, i) * (eyp - ld(1 * nc + n)) - g.rd(1, j) * (exp_ - ld(0 * nc + n));
+  }
+}
+
+// (curl H)_c at E edge (i, j, k) of a 3-component vector field t.
+template <typename T, typename V, typename LD>
+__device__ __forceinline__ V curl_h_at(const Geo<T> &g, LD ld, int c, int i, int j, int k) {
+  const int64_t n = g.id(i, j, k), nc = g.nc;
+  V z(0);
+  if (c == 0) {
+    V hzm = (j > 0) ? ld(2 * nc + g.id(i, j - 1, k)) : z;
+    V hym = (k > 0) ? ld(1 * nc + g.id(i, j, k - 1)) : z;
+    return g.rdd(1, j) * (ld(2 * nc + n) - hzm) - g.rdd(2, k) * (ld(1 * nc + n) - hym);
+  } else if (c == 1) {
+    V hxm = (k > 0) ? ld(0 * nc + g.id(i, j, k - 1)) : z;
+    V hzm = (i > 0) ? ld(2 * nc + g.id(i - 1, j, k)) : z;
+    return g.rdd(2, k) * (ld(0 * nc + n) - hxm) - g.rdd(0, i) * (ld(2 * nc + n) - hzm);
+  } else {
+    V hym = (i > 0) ? ld(1 * nc + g.id(i - 1, j, k)) : z;
+    V hxm = (j > 0) ? ld(0 * nc + g.id(i, j - 1, k)) : z;
+    return g.rdd(0, i) * (ld(1 * nc + n) - hym) - g.rdd(1, j) * (ld(0 * nc + n) - hxm);
+  }
+}
+
+// Per-edge material properties of a grid (computed once, field type T) in
+// g->eprops: E edges: eps (absolute, 0 on dead edges: walls / PEC), sig;
+// H edges: mu (absolute, 0 on dead edges: normal to a wall), sgm; each 3 x nc.
+enum EdgeProp { EP_EPS = 0, EP_SIG = 1, EP_MU = 2, EP_SGM = 3 };
+fdtd_status ensure_edge_props(fdtd_grid *g, cudaStream_t s);
+
+template <typename T>
+Geo<T> make_geo(const fdtd_grid *g) {
+  Geo<T> geo;
+  geo.nx = g->nx; geo.ny = g->ny; geo.nz = g->nz; geo.nc = g->nc;
+  geo.ax = g->axis.as<T>();
+  return geo;
+}
+
+}  // namespace fdtdmor

@@ -46,6 +46,15 @@ class PortDesc(C.Structure):
                 ("w", C.POINTER(C.c_double))]
 
 
+class MorOpts(C.Structure):
+    _fields_ = [("q", C.c_int), ("L", C.c_int), ("M", C.c_double), ("fmax", C.c_double),
+                ("dt0", C.c_double), ("include_center", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int), ("defl_tol", C.c_double), ("orth", C.c_int), ("solver", C.c_int)]
+
+
+MOR_ORTH = {"native": 0, "tf32": 1, "bf16": 2}
+MOR_SOLVER = {"auto": 0, "cgs": 1, "bicgstab": 2}
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -87,6 +96,21 @@ _SIGS = [
     ("fdtd_fields_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_fields_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_launch_count", C.c_int64, [C.c_int]),
+    ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("mor_opts_default", C.c_int, [C.POINTER(MorOpts)]),
+    ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("mor_basis_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_double)]),
+    ("mor_basis_get", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("mor_basis_destroy", C.c_int, [C.c_void_p]),
+    ("mor_project", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("mor_perturb", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_int), C.c_void_p]),
+    ("mor_run", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("mor_model_get", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.c_void_p]),
+    ("mor_model_destroy", C.c_int, [C.c_void_p]),
+    ("mor_compare", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                              C.POINTER(C.c_double), C.c_void_p]),
 ]
 
 
@@ -252,6 +276,133 @@ class Grid:
         check(lib().fdtd_fields_get(self.h, _dptr(out), _stream_ptr(stream)))
         return out
 
+    def edge_props(self, stream=None):
+        """(4, 3, nz, ny, nx): eps, sigma_e on E edges; mu, sigma_m on H edges."""
+        import torch
+        s = self.spec
+        out = torch.empty((4, 3, s.nz, s.ny, s.nx), dtype=self.dtype, device="cuda")
+        check(lib().fdtd_edge_props_get(self.h, _dptr(out), _stream_ptr(stream)))
+        return out
+
     def set_fields(self, f, stream=None):
         f = f.contiguous()
         check(lib().fdtd_fields_set(self.h, _dptr(f), _stream_ptr(stream)))
+
+
+MODEL_FIELDS = {"De": 0, "Dse": 1, "Dm": 2, "Dsm": 3, "K": 4, "Kp": 5, "BE": 6, "CE": 7, "sigma": 8}
+
+
+class Basis:
+    """mor_basis handle: V1 (3nc x q1), V2 (3nc x q2) on the device."""
+
+    def __init__(self, grid: "Grid", q: int, dt0: float, L: int = 2, M: float = 1.1, fmax: float = 0.0,
+                 include_center: bool = True, tol: float = None, maxit: int = 20000,
+                 defl_tol: float = None, orth: str = "native", solver: str = "auto", stream=None,
+                 allow_noconv: bool = False):
+        L_ = lib()
+        o = MorOpts()
+        check(L_.mor_opts_default(C.byref(o)))
+        o.q, o.L, o.M, o.fmax, o.dt0 = int(q), int(L), float(M), float(fmax), float(dt0)
+        o.include_center = 1 if include_center else 0
+        if tol is not None:
+            o.tol = float(tol)
+        o.maxit = int(maxit)
+        if defl_tol is not None:
+            o.defl_tol = float(defl_tol)
+        o.orth = MOR_ORTH[orth]
+        o.solver = MOR_SOLVER[solver]
+        h = C.c_void_p()
+        st = L_.mor_build_basis(grid.h, C.byref(o), _stream_ptr(stream), C.byref(h))
+        self.status = st
+        if st != FDTD_OK and not (allow_noconv and st == FDTD_ENOCONV and h):
+            if h:
+                L_.mor_basis_destroy(h)
+            check(st)
+        self.h = h
+        self.grid = grid
+        _track(self)
+
+    def info(self):
+        q1, q2, it = C.c_int(), C.c_int(), C.c_int()
+        r = C.c_double()
+        check(lib().mor_basis_info(self.h, C.byref(q1), C.byref(q2), C.byref(it), C.byref(r)))
+        return {"q1": q1.value, "q2": q2.value, "max_iters": it.value, "max_resid": r.value}
+
+    def V(self, which: int, stream=None):
+        import torch
+        inf = self.info()
+        q = inf["q1"] if which == 1 else inf["q2"]
+        out = torch.empty((q, 3 * self.grid.spec.ncells), dtype=self.grid.dtype, device="cuda")
+        check(lib().mor_basis_get(self.h, int(which), _dptr(out), _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mor_basis_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """mor_model handle: projected reduced model, perturbation and reduced run."""
+
+    def __init__(self, grid: "Grid", basis: Basis, stream=None):
+        h = C.c_void_p()
+        check(lib().mor_project(grid.h, basis.h, _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.grid = grid
+        _track(self)
+
+    def perturb(self, dt: float, gamma: float = 0.9999, stream=None) -> int:
+        n = C.c_int()
+        check(lib().mor_perturb(self.h, float(dt), float(gamma), C.byref(n), _stream_ptr(stream)))
+        return n.value
+
+    def run(self, u, y=None, reset: bool = True, stream=None, nsteps: int = None):
+        import torch
+        n = int(nsteps if nsteps is not None else u.shape[0])
+        if y is None:
+            y = torch.empty((n, self.grid.p), dtype=self.grid.dtype, device="cuda")
+        check(lib().mor_run(self.h, n, _dptr(u) if self.grid.m else None, _dptr(y) if self.grid.p else None,
+                            1 if reset else 0, _stream_ptr(stream)))
+        return y
+
+    def get(self, name: str, stream=None) -> np.ndarray:
+        which = MODEL_FIELDS[name]
+        r, c = C.c_int(), C.c_int()
+        check(lib().mor_model_get(self.h, which, None, C.byref(r), C.byref(c), _stream_ptr(stream)))
+        out = np.zeros((r.value, c.value), np.float64)
+        if out.size:
+            check(lib().mor_model_get(self.h, which, out.ctypes.data_as(C.POINTER(C.c_double)), None, None,
+                                      _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mor_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def compare(y_red, y_ref, stride: int, offset: int, stream=None) -> float:
+    """Relative L2 error of y_red against rows offset + i*stride of y_ref (device tensors)."""
+    import torch
+    prec = FDTD_F64 if y_red.dtype == torch.float64 else FDTD_F32
+    err = C.c_double()
+    check(lib().mor_compare(_dptr(y_red), _dptr(y_ref), int(y_red.shape[0]), int(stride), int(offset),
+                            int(y_red.shape[1]), prec, C.byref(err), _stream_ptr(stream)))
+    return err.value

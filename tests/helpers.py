@@ -36,18 +36,23 @@ def ragged_grid(nx=41, ny=19, nz=23, seed=101, many_materials=False, magnetic=Tr
     dy = 1e-3 * rng.uniform(0.6, 1.4, ny)
     dz = 1e-3 * rng.uniform(0.3, 1.4, nz)
     g = W.GridSpec(nx, ny, nz, dx, dy, dz, eps, mu, se, sm, pec, mat)
-    # a line source in x crossing the tile border at i = 32, a y-line crossing j = 8/16
-    ks = np.full(12, nz // 2); js = np.full(12, 8); is_ = np.arange(26, 38)
+    # a line source in x crossing the tile border at i = 32, a y-line crossing
+    # j = 8 / 16 (positions clipped into smaller grids)
+    def ci(v, n):
+        return int(min(max(v, 1), n - 2))
+    is_ = np.arange(ci(26, nx), ci(38, nx) + 1)
+    ks = np.full(is_.size, nz // 2); js = np.full(is_.size, ci(8, ny))
     g.ports.append(W.Port(W.COMP_EZ, ks.astype(np.int64), js.astype(np.int64), is_.astype(np.int64),
-                          rng.uniform(0.5, 1.5, 12)))
-    js2 = np.arange(4, 18)
-    g.ports.append(W.Port(W.COMP_EX, np.full(js2.size, 5, np.int64), js2.astype(np.int64),
-                          np.full(js2.size, 32, np.int64), np.ones(js2.size)))
-    g.ports.append(W.Port.point(W.COMP_EY, 32, 16, 11, 2.0))
+                          rng.uniform(0.5, 1.5, is_.size)))
+    js2 = np.arange(ci(4, ny), ci(18, ny) + 1)
+    g.ports.append(W.Port(W.COMP_EX, np.full(js2.size, ci(5, nz), np.int64), js2.astype(np.int64),
+                          np.full(js2.size, ci(32, nx), np.int64), np.ones(js2.size)))
+    g.ports.append(W.Port.point(W.COMP_EY, ci(32, nx), ci(16, ny), ci(11, nz), 2.0))
     for c, (i, j, k) in enumerate([(31, 7, 12), (32, 8, 12), (5, 17, 20), (40, 18, 1)]):
-        g.probes.append(W.Port.point(c % 3, i, j, k))
-    g.probes.append(W.Port(W.COMP_EZ, np.full(5, 9, np.int64), np.arange(5, 10, dtype=np.int64),
-                           np.full(5, 20, np.int64), np.full(5, 0.2)))
+        g.probes.append(W.Port.point(c % 3, ci(i, nx), ci(j, ny), ci(k, nz)))
+    js3 = np.arange(ci(5, ny), ci(10, ny))
+    g.probes.append(W.Port(W.COMP_EZ, np.full(js3.size, ci(9, nz), np.int64), js3.astype(np.int64),
+                           np.full(js3.size, ci(20, nx), np.int64), np.full(js3.size, 0.2)))
     return g
 
 
