@@ -76,35 +76,32 @@ def cav10():
     return wl, s, dt0, ob, grid, gb
 
 
-def test_basis_matches_oracle_f64(cav10):
-    """Orthonormal bases spanning the oracle's subspaces.  A pool vector kept
-    with new content r (relative to its norm) has its direction fixed only to
-    (solve error)/r, so exact column parity is well posed only when every kept
-    vector has substantial new content: the comparison uses a deflation
-    tolerance of 1e-3 on both sides (the default 1e-8 run is checked through
-    its invariants: moments and probe waveforms)."""
-    wl, s, dt0, ob_default, grid, gb_default = cav10
-    ob = mor.sprim_basis(s, dt0, wl.q, wl.L, wl.M, wl.fmax, defl_tol=1e-3)
-    gb = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=1e-13, defl_tol=1e-3)
+@pytest.mark.parametrize("q,L,center", [(6, 0, True), (8, 1, False)])
+def test_basis_matches_oracle_f64(cav10, q, L, center):
+    """Columns of V1, V2 against the oracle for short chains (a real point with
+    six moments; the complex pair with two).  Each chain vector is the small
+    remainder of A^{-1}(R+F) q after orthogonalisation, so solve error grows by
+    the inverse of that remainder at every moment: exact column parity is only
+    well posed for short chains; the long multi-point chains of the default
+    settings are checked through their invariants (moments, waveforms)."""
+    wl, s, dt0, _, grid, _ = cav10
+    ob = mor.sprim_basis(s, dt0, q, L, wl.M, wl.fmax, include_center=center, defl_tol=1e-6)
+    gb = F.Basis(grid, q, dt0, L, wl.M, wl.fmax, include_center=center, tol=1e-13, defl_tol=1e-6)
     inf = gb.info()
-    assert inf["max_resid"] <= 1e-13
+    assert inf["max_resid"] <= 2e-13
     V1 = _vectors_to_oracle(s, gb.V(1).cpu().numpy(), "E")
     V2 = _vectors_to_oracle(s, gb.V(2).cpu().numpy(), "H")
-    # dead edges carry exactly zero
     full1 = gb.V(1).cpu().numpy().reshape(inf["q1"], 3, *s.shape)
     for c in range(3):
-        assert np.all(full1[:, c][:, ~s.e_mask[c]] == 0)
+        assert np.all(full1[:, c][:, ~s.e_mask[c]] == 0)   # dead edges carry exactly zero
     assert np.max(np.abs(V1.T @ V1 - np.eye(V1.shape[1]))) < 1e-12
     assert np.max(np.abs(V2.T @ V2 - np.eye(V2.shape[1]))) < 1e-12
-    # same subspaces as the oracle: principal angles between the spans (the
-    # deflation of a borderline vector may differ, so allow one direction)
     for Vg, Vo in ((V1, ob.V1), (V2, ob.V2)):
         cosines = np.linalg.svd(Vg.T @ Vo, compute_uv=False)
         msg = f"q gpu {Vg.shape[1]} oracle {Vo.shape[1]}, cosines {np.round(cosines, 9)}"
         assert Vg.shape[1] == Vo.shape[1], msg
-        assert cosines.min() > 1 - 1e-6, msg
-        # same pool order and CGS2: columns agree up to rounding
-        assert np.max(np.abs(Vg - Vo)) < 1e-5, msg
+        assert cosines.min() > 1 - 1e-8, msg
+        assert np.max(np.abs(Vg - Vo)) < 1e-5, msg   # same pool order and CGS2
 
 
 def test_projection_kernel_matches_oracle_on_gpu_basis(cav10):
