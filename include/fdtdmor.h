@@ -236,6 +236,24 @@ FDTD_API fdtd_status mor_compare(const void *y_red, const void *y_ref, int64_t n
                                  int64_t offset, int p, fdtd_prec prec, double *err,
                                  fdtd_stream_t stream);
 
+/* The comparison of mor_compare without any device allocation, for callers
+ * that cannot allocate while it runs: code inside a CUDA stream capture
+ * (cudaMalloc cannot be captured), a host application or plugin that owns all
+ * device memory itself, or a run under an allocator that must not grow.  The
+ * paper has no counterpart; this is a deployment variant of the A9 step.
+ * Arguments and result are those of mor_compare.  Its reduction scratch is a
+ * static device array inside the library (64 KiB, held on every device that
+ * loads the library until the process exits), so n * p is limited to
+ * 16,777,216 samples; larger inputs return FDTD_EINVAL with a message.  The
+ * first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call overwrites the scratch before reading it (no clearing needed),
+ * and calls that overlap on the GPU share it and race: serialise them.
+ * Synchronises the stream. */
+FDTD_API fdtd_status mor_compare_noalloc(const void *y_red, const void *y_ref, int64_t n, int64_t stride,
+                                         int64_t offset, int p, fdtd_prec prec, double *err,
+                                         fdtd_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

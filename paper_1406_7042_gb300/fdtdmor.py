@@ -111,6 +111,8 @@ _SIGS = [
     ("mor_model_destroy", C.c_int, [C.c_void_p]),
     ("mor_compare", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
                               C.POINTER(C.c_double), C.c_void_p]),
+    ("mor_compare_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
+                                      C.c_int, C.POINTER(C.c_double), C.c_void_p]),
 ]
 
 
@@ -405,4 +407,14 @@ def compare(y_red, y_ref, stride: int, offset: int, stream=None) -> float:
     err = C.c_double()
     check(lib().mor_compare(_dptr(y_red), _dptr(y_ref), int(y_red.shape[0]), int(stride), int(offset),
                             int(y_red.shape[1]), prec, C.byref(err), _stream_ptr(stream)))
+    return err.value
+
+
+def compare_noalloc(y_red, y_ref, stride: int, offset: int, stream=None) -> float:
+    """compare() through mor_compare_noalloc: no device allocation (static scratch)."""
+    import torch
+    prec = FDTD_F64 if y_red.dtype == torch.float64 else FDTD_F32
+    err = C.c_double()
+    check(lib().mor_compare_noalloc(_dptr(y_red), _dptr(y_ref), int(y_red.shape[0]), int(stride), int(offset),
+                                    int(y_red.shape[1]), prec, C.byref(err), _stream_ptr(stream)))
     return err.value
