@@ -159,20 +159,43 @@ def run_ours(args):
     wl = _workload()
     g = wl.grid
     grid = F.Grid(g, "f32")
-    dt = wl.s_ref * grid.cfl_dt()
+    dt0 = wl.s_ref * grid.cfl_dt()
     nref = int(args.fdtd_steps or wl.nsteps_ref)
-    u_np = W.excitation(g, wl.f0, wl.bw, dt, nref).astype(np.float32)
+    kred = int(round(wl.s_red[0] / wl.s_ref))          # 20x CFL -> dt = 20 dt0
+    dtr = kred * dt0
+    nred = min(wl.nsteps_red[0], nref // kred)
+    u_np = W.excitation(g, wl.f0, wl.bw, dt0, nref).astype(np.float32)
     u = torch.tensor(u_np, device="cuda")
+    ur = torch.tensor(W.excitation(g, wl.f0, wl.bw, dtr, nred).astype(np.float32), device="cuda")
     y = torch.empty((nref, grid.p), dtype=torch.float32, device="cuda")
+    yr = torch.empty((nred, grid.p), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    state = {}
 
-    def one_step(ev_pair=None):
-        if ev_pair:
-            ev_pair[0].record(stream)
-        grid.step(dt, u, y, reset=True)
-        if ev_pair:
-            ev_pair[1].record(stream)
+    def one_step(rec=None):
+        """One pass of the hot path: full-order reference run, basis, projection,
+        perturbation at the reduced step, reduced run, probe comparison."""
+        e = [ev() for _ in range(7)]
+        e[0].record(stream)
+        grid.step(dt0, u, y, reset=True)
+        e[1].record(stream)
+        if args.mor:
+            basis = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=args.tol, defl_tol=args.defl_tol,
+                            allow_noconv=True)
+            e[2].record(stream)
+            model = F.Model(grid, basis)
+            e[3].record(stream)
+            model.perturb(dtr)
+            e[4].record(stream)
+            model.run(ur, yr, reset=True)
+            e[5].record(stream)
+            err = F.compare(yr, y, stride=kred, offset=kred - 1)
+            e[6].record(stream)
+            state.update(basis=basis, model=model, err=err)
+        if rec is not None:
+            rec.append(e)
 
     for _ in range(args.warmup):
         one_step()
@@ -184,68 +207,97 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     F.launch_count(reset=True)
-    evs = []
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    recs = []
+    t_start, t_end = ev(), ev()
     torch.cuda.synchronize()
     t_start.record(stream)
     for _ in range(args.steps):
-        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        one_step(e)
-        evs.append(e)
+        one_step(recs)
         flush.zero_()
     t_end.record(stream)
     torch.cuda.synchronize()
     launches = F.launch_count(reset=True)
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    fdtd_ms = [a.elapsed_time(b) for a, b in evs]
+    fdtd_ms = sum(r[0].elapsed_time(r[1]) for r in recs)
+    stage = {}
+    if args.mor:
+        names = ["basis", "project", "perturb", "run", "compare"]
+        for q, nm in enumerate(names):
+            stage[nm + "_ms"] = round(sum(r[q + 1].elapsed_time(r[q + 2]) for r in recs) / args.steps, 3)
     if world > 1:
-        tt = torch.tensor([total_ms, sum(fdtd_ms)], device="cuda")
+        tt = torch.tensor([total_ms, fdtd_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, fsum = tt.tolist()
-    else:
-        fsum = sum(fdtd_ms)
+        total_ms, fdtd_ms = tt.tolist()
     cells = g.ncells * nref * args.steps * world
-    value = cells / (fsum / 1e3) / 1e6
+    value = cells / (fdtd_ms / 1e3) / 1e6
     # end-to-end through the host-buffer entry point
     uh = torch.tensor(u_np).pin_memory()
     yh = torch.empty((nref, grid.p), dtype=torch.float32).pin_memory()
-    grid.step_host(dt, uh, yh, reset=True)
+    grid.step_host(dt0, uh, yh, reset=True)
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
-        grid.step_host(dt, uh, yh, reset=True)
+        grid.step_host(dt0, uh, yh, reset=True)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": round(g.ncells * nref / e2e_s / 1e6, 1), "unit": "Mcell-updates/s",
-           "h2d_bytes_per_step": int(uh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)}
+           "h2d_bytes_per_step": int(uh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4),
+           "path": "fdtd_step_host (pinned host u -> device, steps, device y -> pinned host)"}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    per_launch_ms = fsum / (nref * args.steps)
+    per_launch_ms = fdtd_ms / (nref * args.steps)
     achieved = BYTES_PER_CELL_F32 * g.ncells / (per_launch_ms / 1e3) / 1e9
     roof = {"kernel": "yee_fused_kernel<float,uint8,homog_h>", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+            "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks
+            else "of fallback 6.8 TB/s",
             "note": "64^3 state (25 MB both buffers) is L2-resident; algorithmic 49 B/cell-update"}
-    extra = {}
-    if args.hbm_grid and rank == 0:
-        extra["yee_hbm"] = hbm_grid_measure(F, W, hbm)
     line = {"metric": "Yee Mcell-updates/s", "value": round(value, 1), "unit": "Mcell-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "fdtd_steps_per_bench_step": nref,
-                       "s": wl.s_ref, "dt_s": dt, "l2": "flushed (512 MB write) between bench steps; the 64^3 state is L2-resident inside a step",
+                       "s": wl.s_ref, "dt_s": dt0, "q": wl.q, "L": wl.L, "M": wl.M, "fmax_hz": wl.fmax,
+                       "s_reduced": wl.s_red[0], "reduced_steps": nred, "cgs_tol": args.tol,
+                       "l2": "flushed (512 MB write) between bench steps; the 64^3 state is L2-resident inside a step",
                        "value_is": "cell-updates of fdtd_step / its CUDA-event time inside the timed steps"},
             "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
-    line.update(extra)
+    if args.mor:
+        red_ms = sum(stage[k] for k in ("basis_ms", "project_ms", "perturb_ms", "run_ms"))
+        inf = state["basis"].info()
+        line["reduce_run"] = dict(stage, reduce_run_ms=round(red_ms, 3),
+                                  fdtd_ms=round(fdtd_ms / args.steps, 3),
+                                  speedup_vs_fdtd=round((fdtd_ms / args.steps) / red_ms, 4),
+                                  probe_err_vs_fdtd=round(state["err"], 6), q1=inf["q1"], q2=inf["q2"],
+                                  max_solver_iters=inf["max_iters"], max_rel_residual=inf["max_resid"])
+        line["reduce_run"]["accuracy_by_s"] = accuracy_sweep(F, W, wl, grid, state["model"], y, dt0, nref)
+    if rank == 0 and args.hbm_grid:
+        line["yee_hbm"] = hbm_grid_measure(F, W, hbm)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(wl, dt, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(wl, dt0, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def accuracy_sweep(F, W, wl, grid, model, yref, dt0, nref):
+    """Probe error of the reduced model against the full-order run, at several
+    CFL factors s = 0.99 k (outside the timed region)."""
+    import torch
+    out = {}
+    for k in (1, 2, 4, 20):
+        dt = k * dt0
+        model.perturb(dt)
+        ns = nref // k
+        uu = torch.tensor(W.excitation(wl.grid, wl.f0, wl.bw, dt, ns), dtype=torch.float32, device="cuda")
+        yr = model.run(uu)
+        n20 = max(1, ns // 5)
+        out[f"s={round(0.99 * k, 2)}"] = {"err_full_window": round(F.compare(yr, yref, k, k - 1), 6),
+                                          "err_first_20pct": round(F.compare(yr[:n20].contiguous(), yref, k, k - 1), 6),
+                                          "steps": ns}
+    return out
 
 
 def hbm_grid_measure(F, W, hbm, nsteps=200):
@@ -299,7 +351,7 @@ def only_yee(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fdtd-steps", type=int, default=0, help="override full-order steps per bench step")
@@ -307,6 +359,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hbm-grid", type=int, default=1)
+    ap.add_argument("--mor", type=int, default=1, help="include the reduction stages in the bench step")
+    ap.add_argument("--tol", type=float, default=1e-4, help="shifted-solve residual limit (Sec. IV-B: 1e-4)")
+    ap.add_argument("--defl-tol", type=float, default=1e-5)
     ap.add_argument("--only-yee", default="", choices=["", "graded", "metascreen", "cavity10"])
     ap.add_argument("--yee-steps", type=int, default=20)
     args = ap.parse_args()

@@ -251,6 +251,34 @@ static fdtd_status to_run_type(cudaStream_t s, const double *X, int n, DevBuf &d
 
 fdtd_status to_run_type_dispatch(mor_model *M, const double *X, int n, DevBuf &dst, cudaStream_t s);
 
+__global__ void count_nonfinite_kernel(const double *__restrict__ x, int n, int *bad) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    if (!isfinite(x[t])) atomicAdd(bad, 1);
+}
+
+// The projected matrices must be finite before they are factorised.
+static fdtd_status check_finite(mor_model *M, cudaStream_t s) {
+  DevBuf bad;
+  FDTD_CHECK(bad.alloc(sizeof(int), s));
+  FDTD_CHECK_CUDA(cudaMemsetAsync(bad.ptr, 0, sizeof(int), s));
+  const DevBuf *mats[] = {&M->De, &M->Dse, &M->Dm, &M->Dsm, &M->K};
+  const int sizes[] = {M->q1 * M->q1, M->q1 * M->q1, M->q2 * M->q2, M->q2 * M->q2, M->q1 * M->q2};
+  for (int i = 0; i < 5; ++i) {
+    if (sizes[i] == 0) continue;
+    count_nonfinite_kernel<<<std::min(1024, (sizes[i] + 255) / 256), 256, 0, s>>>(mats[i]->as<double>(), sizes[i], bad.as<int>());
+    FDTD_CHECK(after_launch("count_nonfinite_kernel"));
+  }
+  int h = 0;
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(&h, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  bad.release(s);
+  if (h) {
+    set_error("the reduced matrices hold %d non-finite entries (a shifted solve diverged)", h);
+    return FDTD_EUNSTABLE;
+  }
+  return FDTD_OK;
+}
+
 static fdtd_status perturb_and_prepare(mor_model *M, double dt, double gamma, int *n_clipped, cudaStream_t s) {
   const int q1 = M->q1, q2 = M->q2, m = M->m, p = M->p;
   Dense D{s};
@@ -268,6 +296,7 @@ static fdtd_status perturb_and_prepare(mor_model *M, double dt, double gamma, in
   // ---- Sec. III-A step 1: factors and M = Le^{-1} K~ Lm^{-T}, SVD
   FDTD_CHECK_CUDA(cudaMemcpyAsync(Le, M->De.ptr, sizeof(double) * q1 * q1, cudaMemcpyDeviceToDevice, s));
   FDTD_CHECK_CUDA(cudaMemcpyAsync(Lm, M->Dm.ptr, sizeof(double) * q2 * q2, cudaMemcpyDeviceToDevice, s));
+  FDTD_CHECK(check_finite(M, s));
   FDTD_CHECK(D.chol(Le, q1, dinfo, "D~eps"));
   FDTD_CHECK(D.chol(Lm, q2, dinfo, "D~mu"));
   int ncl = 0;
@@ -285,8 +314,10 @@ static fdtd_status perturb_and_prepare(mor_model *M, double dt, double gamma, in
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_svd_kernel, 256, 0);
     const int npairs = (q2 + 1) / 2;
     int blocks = std::max(1, std::min((npairs + 7) / 8, std::max(1, per) * nsm));
-    double tol = 1e-15;
-    int maxsw = 60;
+    // rotation threshold: a few ulps times sqrt(rows) (pairs closer to orthogonal
+    // than rounding can certify are left alone)
+    double tol = std::max(1e-12, 4.0 * 2.220446049250313e-16 * std::sqrt((double)q1));
+    int maxsw = 80;
     unsigned *fl = flag.as<unsigned>();
     int mm = q1, nn = q2;
     void *args[] = {&Mc, &mm, &nn, &Wc, &tol, &maxsw, &fl};

@@ -380,7 +380,7 @@ __global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict
       } else if (mode == SM_CGS_RHO || mode == SM_BICG_RHO) {
         s.rn2 = acc[2];
         s.iters += 1;
-        if (!isfinite(acc[2])) breakdown();
+        if (!isfinite(acc[2]) || acc[2] > 1e16 * s.bn2) breakdown();   // diverged
         else if (sqrt(acc[2]) <= tol * sqrt(s.bn2)) s.active = 0;
         else if (s.iters >= maxit) { s.status = 1; s.active = 0; }
         else if (norm2(rho) == 0) breakdown();
@@ -648,6 +648,9 @@ struct BasisBuilder {
   int max_iters = 0;
   double max_resid = 0;
   bool noconv = false;
+  bool last_failed = false;
+  int fallbacks = 0;
+  std::vector<int> rhs_failed;  // per right-hand side, of the last solve
 
   BasisBuilder(fdtd_grid *g_, const mor_opts &o_, cudaStream_t s_) : g(g_), o(o_), s(s_) {
     nc = g->nc;
@@ -656,8 +659,24 @@ struct BasisBuilder {
 
   // Solve A(z_b) x = (R+F) v for every active right-hand side b (x = [x1; x2]
   // written to out, nb x 6nc).  v: nb x 6nc.
+  // AUTO: the paper's CGS on FP64 grids, falling back to BiCGSTAB for the whole
+  // block when a right-hand side fails; BiCGSTAB on FP32 grids.
   fdtd_status solve(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
                     const cplx<T> *vin, cplx<T> *out) {
+    if (o.solver != MOR_SOLVER_AUTO) return solve_with(w, zs, from_b, vin, out, o.solver);
+    if (g->prec != FDTD_F64) return solve_with(w, zs, from_b, vin, out, MOR_SOLVER_BICGSTAB);
+    const bool nc0 = noconv;
+    const int it0 = max_iters;
+    const double r0 = max_resid;
+    FDTD_CHECK(solve_with(w, zs, from_b, vin, out, MOR_SOLVER_CGS));
+    if (!last_failed) return FDTD_OK;
+    noconv = nc0; max_iters = it0; max_resid = r0;
+    fallbacks += 1;
+    return solve_with(w, zs, from_b, vin, out, MOR_SOLVER_BICGSTAB);
+  }
+
+  fdtd_status solve_with(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
+                         const cplx<T> *vin, cplx<T> *out, int solver) {
     const int nb = (int)zs.size();
     const int64_t n3 = 3 * nc, n6 = 6 * nc;
     std::vector<std::complex<double>> one(nb, 1.0), negz(nb), zz(zs);
@@ -687,8 +706,6 @@ struct BasisBuilder {
     std::vector<CgsScal> hsc(nb);
     for (auto &x : hsc) { x = CgsScal{}; x.active = 1; }
     const bool trace = getenv("FDTDMOR_TRACE") != nullptr;
-    const int solver = o.solver == MOR_SOLVER_AUTO ? (g->prec == FDTD_F64 ? MOR_SOLVER_CGS : MOR_SOLVER_BICGSTAB)
-                                                   : o.solver;
     FDTD_CHECK_CUDA(cudaMemcpyAsync(sc, hsc.data(), sizeof(CgsScal) * nb, cudaMemcpyHostToDevice, s));
     cplx<T> *P = w.P.template as<cplx<T>>(), *x = w.x.template as<cplx<T>>(), *rr = w.rr.template as<cplx<T>>();
     cplx<T> *rt = w.rt.template as<cplx<T>>(), *u = w.u.template as<cplx<T>>(), *p = w.p.template as<cplx<T>>();
@@ -789,10 +806,13 @@ struct BasisBuilder {
     }
     FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
     FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
-    for (auto &x2 : hsc) {
+    last_failed = false;
+    rhs_failed.assign(nb, 0);
+    for (int b = 0; b < nb; ++b) {
+      const CgsScal &x2 = hsc[b];
       max_iters = std::max(max_iters, x2.iters);
       if (x2.bn2 > 0) max_resid = std::max(max_resid, std::sqrt(x2.rn2 / x2.bn2));
-      if (x2.status != 0 || x2.active) noconv = true;
+      if (x2.status != 0 || x2.active) { noconv = true; last_failed = true; rhs_failed[b] = 1; }
     }
     // out = [x1; x2], x2 = (r2 - z curlE(x1)) / a22
     for (int b = 0; b < nb; ++b) {
@@ -904,12 +924,22 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
   }
   // dead source edges (PEC) must carry no right-hand side: r1 is masked by
   // e_from_h (A = r1 only on live edges), so nothing else to do here.
+  // a chain whose shifted solve failed ends there: its vector does not enter
+  // the pool, and its later right-hand sides are zero (skipped by the solver)
+  std::vector<int> dead(nb, 0);
   for (int j = 0; j < k; ++j) {
+    for (int b = 0; b < nb; ++b)
+      if (dead[b]) {
+        cplx<T> *src = j == 0 ? w.r.template as<cplx<T>>() : w.v.template as<cplx<T>>();
+        FDTD_CHECK_CUDA(cudaMemsetAsync(src + (size_t)b * n6, 0, cb * n6, s));
+      }
     FDTD_CHECK(bb.solve(w, zs, j == 0, w.v.template as<cplx<T>>(), X));
+    for (int b = 0; b < nb; ++b) dead[b] |= bb.rhs_failed.empty() ? 0 : bb.rhs_failed[b];
     // block Arnoldi per point: each new column against the whole chain
     for (int c = 0; c < m; ++c) {
       for (int pidx = 0; pidx < np; ++pidx) {
         const int b = pidx * m + c;
+        if (dead[b]) continue;
         cplx<T> *vec = X + (size_t)b * n6;
         cplx<T> *chain = Qc + (size_t)pidx * clen * n6;
         double n0, n1;

@@ -210,9 +210,13 @@ def cavity_graded(n: int = 64, seed: int = SEED_BASE + 2, nblocks: int = 16,
 
 
 def config2(seed: int = SEED_BASE + 2, n: int = 64) -> Workload:
+    """64^3 graded cavity.  Its 0.163 ps step puts the whole 5-15 GHz band on an
+    arc of 2 pi fmax dt0 = 0.0154 rad of the unit circle, so the expansion
+    radius is taken as 1 + pi fmax dt0 = 1.0077 (half that arc away from the
+    circle) instead of 1.1, which would sit 13 arcs away."""
     g = cavity_graded(n, seed)
     return Workload(f"graded_cavity{n}_f32", g, 0.99, 400000, 10e9, 10e9, q=200, L=2,
-                    M=1.1, fmax=15e9, s_red=[19.8], nsteps_red=[20000], precision="f32")
+                    M=1.0077, fmax=15e9, s_red=[19.8], nsteps_red=[20000], precision="f32")
 
 
 # ---------------------------------------------------------------- config 3
