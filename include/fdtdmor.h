@@ -97,7 +97,7 @@ FDTD_API fdtd_status fdtd_set_allocator(fdtd_alloc_fn alloc, fdtd_free_fn releas
 FDTD_API const char *fdtd_last_error(void);
 
 /* A1 -- grid and material setup (Sec. II-A): copies the descriptor, uploads
- * the per-cell material ids (uint8 when nmat <= 256, else uint16), derives the
+ * the per-cell material ids (uint8 when nmat <= 255, else uint16), derives the
  * per-axis spacing tables and the per-material update coefficients on the
  * device, and zeroes the fields.  m sources, p probes. */
 FDTD_API fdtd_status fdtd_grid_create(const fdtd_grid_desc *desc, int m, const fdtd_port *ports,
@@ -110,9 +110,32 @@ FDTD_API fdtd_status fdtd_grid_destroy(fdtd_grid *grid);
  * axis.  Returns a negative value for a NULL grid. */
 FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
 
+/* Kernel form of the leap-frog (A2).  All forms compute the same update.
+ * AUTO: SPLIT.  PERSIST: one launch runs up to 8192 steps in place; its CTAs
+ * take (step, half step, z slab, tile) work units in order from a counter and
+ * wait (bounded) only for the slabs a unit depends on, so the E and H halves of
+ * a slab meet in L2.  SPLIT: an E launch and an H launch per step, each thread
+ * updating 4 (FP32) or 2 (FP64) consecutive x cells with vector loads when nx
+ * allows.  TMA: one
+ * fused launch per step staging planes through shared memory with the tensor
+ * memory accelerator (needs nx a multiple of 16 for uint8 ids, 8 for uint16).
+ * FUSED: one fused launch per step with plain loads into shared memory. */
+typedef enum {
+  FDTD_KERNEL_AUTO = 0,
+  FDTD_KERNEL_PERSIST = 1,
+  FDTD_KERNEL_SPLIT = 2,
+  FDTD_KERNEL_TMA = 3,
+  FDTD_KERNEL_FUSED = 4
+} fdtd_kernel;
+
+/* Choose the kernel form for later fdtd_step calls on this grid.
+ * FDTD_EINVAL for an unknown value or TMA on a grid it cannot serve. */
+FDTD_API fdtd_status fdtd_grid_set_kernel(fdtd_grid *grid, int kernel);
+
 /* A2 -- full-order leap-frog, Eq. (matrix) / (MNAform), nsteps steps of dt:
  * E^{n+1} = Ca E^n + Cb (curl H^{n+1/2} - w u^{n+1}),
- * H^{n+3/2} = Da H^{n+1/2} - Db curl E^{n+1}, fused in one kernel per step.
+ * H^{n+3/2} = Da H^{n+1/2} - Db curl E^{n+1}, in the form fdtd_grid_set_kernel
+ * chose.
  * u: device [nsteps][m], row n = u^{n+1}; y: device [nsteps][p], row n =
  * probes of E^{n+1} (zeroed by the call).  reset_fields != 0 zeroes the state
  * first; otherwise the state continues from the previous call. */
@@ -124,6 +147,12 @@ FDTD_API fdtd_status fdtd_step(fdtd_grid *grid, double dt, int64_t nsteps, const
  * y_host should be pinned for the copies to be asynchronous. */
 FDTD_API fdtd_status fdtd_step_host(fdtd_grid *grid, double dt, int64_t nsteps, const void *u_host,
                            void *y_host, int reset_fields, fdtd_stream_t stream);
+
+/* Synchronise the stream and report FDTD_ETIMEOUT if a bounded device-side wait
+ * of an earlier fdtd_step on this grid gave up (the flag is then cleared): an
+ * mbarrier wait of the TMA form, or a grid barrier of the persistent form
+ * (about one second each).  The fields are then undefined. */
+FDTD_API fdtd_status fdtd_check(fdtd_grid *grid, fdtd_stream_t stream);
 
 /* Copy the six field arrays (Ex, Ey, Ez, Hx, Hy, Hz, each nx*ny*nz of the
  * handle's type, contiguous) to / from the device buffer fields6. */

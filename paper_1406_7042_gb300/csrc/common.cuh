@@ -116,6 +116,13 @@ struct fdtd_grid {
   double ctab_dt = -1;
   fdtdmor::TileLists lists;
   fdtdmor::DevBuf u_stage, y_stage;  // device staging for fdtd_step_host
+  fdtdmor::DevBuf gsync;        // ticket and per-slab completion counters of the dataflow kernel
+  int kernel = 0;               // fdtd_kernel chosen by fdtd_grid_set_kernel (0 = automatic)
+  fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
+  bool emat_ready = false;
+  fdtdmor::DevBuf uflag;        // per (tile, plane) uniform material id or -1 (fast Yee kernel)
+  bool uflag_ready = false;
+  fdtdmor::DevBuf errflag;      // set by kernels whose bounded device waits gave up
   fdtdmor::DevBuf eprops;       // per-edge eps, sig (E) and mu, sgm (H), 4 x 3 x nc (reduction kernels)
   bool eprops_ready = false;
   cudaStream_t create_stream = nullptr;

@@ -177,7 +177,7 @@ fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *po
   g->prec = d->prec;
   g->elem = d->prec == FDTD_F64 ? 8 : 4;
   g->nmat = d->nmat;
-  g->id_bytes = d->nmat <= 256 ? 1 : 2;
+  g->id_bytes = d->nmat <= 255 ? 1 : 2;   // the largest id value is kept free as a sentinel
   g->create_stream = s;
   auto fail = [&](fdtd_status st) { fdtd_grid_destroy(g); return st; };
   g->dx.assign(d->dx, d->dx + d->nx);
@@ -230,6 +230,8 @@ fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *po
   }
   if (cudaMemsetAsync(g->fields[0].ptr, 0, fbytes, s) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "memset"));
   if ((st = g->mat.alloc((size_t)g->nc * g->id_bytes, s)) != FDTD_OK) return fail(st);
+  if ((st = g->errflag.alloc(sizeof(unsigned), s)) != FDTD_OK) return fail(st);
+  if (cudaMemsetAsync(g->errflag.ptr, 0, sizeof(unsigned), s) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "memset"));
   if (g->id_bytes == 2) {
     if (cudaMemcpyAsync(g->mat.ptr, d->mat_id, g->nc * 2, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return fail(cuda_fail(cudaGetLastError(), "upload mat_id"));
@@ -298,12 +300,30 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->u_stage.release(s);
   g->y_stage.release(s);
   g->eprops.release(s);
+  g->errflag.release(s);
+  g->uflag.release(s);
+  g->emat.release(s);
+  g->gsync.release(s);
   cudaStreamSynchronize(s);
   delete g;
   return FDTD_OK;
 }
 
 double fdtd_cfl_dt(const fdtd_grid *g) { return g ? g->cfl : -1.0; }
+
+fdtd_status fdtd_check(fdtd_grid *g, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g, "fdtd_check: NULL grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned h = 0;
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(&h, g->errflag.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    FDTD_CHECK_CUDA(cudaMemsetAsync(g->errflag.ptr, 0, sizeof(unsigned), s));
+    set_error("a bounded device-side wait of the stepping kernel gave up; the fields are not valid");
+    return FDTD_ETIMEOUT;
+  }
+  return FDTD_OK;
+}
 
 fdtd_status fdtd_fields_get(const fdtd_grid *g, void *fields6, fdtd_stream_t stream) {
   FDTD_REQUIRE(g && fields6, "fdtd_fields_get: NULL argument");

@@ -72,7 +72,6 @@ __global__ void kv_kernel(Geo<T> g, const T *__restrict__ ep, const T *__restric
 
 constexpr int GT = 32;   // output tile
 constexpr int GK = 32;   // rows per smem stage
-constexpr int GSLICE = 4096;  // rows per CTA slice (FP32 accumulation span)
 
 // partial[s][a][b] = sum over rows of slice s of A[a][r] w[r] B[b][r]
 template <typename T>

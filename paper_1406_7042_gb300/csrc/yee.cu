@@ -15,84 +15,17 @@
 // cells (the non-uniform, inhomogeneous reading of Sec. II-A).
 #include <algorithm>
 
+#include <string>
+
 #include "common.cuh"
 #include "grid_internal.cuh"
+#include "yee_internal.cuh"
 
 namespace fdtdmor {
 
 constexpr int YTX = 32, YTY = 8, YNT = YTX * YTY;
 constexpr int YEX = YTX + 1, YEY = YTY + 1;   // E region: tile + high halo
 constexpr int YHX = YTX + 2, YHY = YTY + 2;   // H / id region: tile + both halos
-
-template <typename T, typename ID>
-struct YeeArgs {
-  int nx, ny, nz, kchunk;
-  int64_t nc;
-  const T *__restrict__ Ein;   // 3 components, stride nc
-  const T *__restrict__ Hin;
-  T *__restrict__ Eout;
-  T *__restrict__ Hout;
-  const ID *__restrict__ mat;
-  const T *__restrict__ ax;    // axis tables (AX_COUNT x (nx+ny+nz))
-  const T *__restrict__ mtab;  // eps, sig, mu, sigm, pec (5 x nmat)
-  const T *__restrict__ ctab;  // ca, cb, da, db (4 x nmat)
-  int nmat;
-  T inv_dt;
-  const int32_t *__restrict__ src_ptr;
-  const PortEntry *__restrict__ src;
-  const T *__restrict__ u;     // row of this step: u[port]
-  const int32_t *__restrict__ prb_ptr;
-  const PortEntry *__restrict__ prb;
-  T *__restrict__ y;           // row of this step: y[probe]
-};
-
-template <typename T>
-__device__ __forceinline__ T axv(const T *ax, int ntot, int table, int idx) {
-  return __ldg(ax + table * ntot + idx);
-}
-
-// (Ca, Cb) of an E edge from the four cells around it (c00: lo/lo, c10: hi/lo,
-// c01: lo/hi, c11: hi/hi along the two transverse axes) and their weights.
-template <typename T, typename ID>
-__device__ __forceinline__ void e_coef(const YeeArgs<T, ID> &a, ID c00, ID c10, ID c01, ID c11,
-                                       T wa_lo, T wa_hi, T wb_lo, T wb_hi, T &ca, T &cb) {
-  if (c00 == c10 && c00 == c01 && c00 == c11) {
-    ca = __ldg(a.ctab + c00);
-    cb = __ldg(a.ctab + a.nmat + c00);
-    return;
-  }
-  const T *pec = a.mtab + 4 * a.nmat;
-  if (__ldg(pec + c00) != T(0) || __ldg(pec + c10) != T(0) || __ldg(pec + c01) != T(0) ||
-      __ldg(pec + c11) != T(0)) {
-    ca = T(0);
-    cb = T(0);
-    return;
-  }
-  const T *eps = a.mtab, *sig = a.mtab + a.nmat;
-  T w00 = wa_lo * wb_lo, w10 = wa_hi * wb_lo, w01 = wa_lo * wb_hi, w11 = wa_hi * wb_hi;
-  T e = w00 * __ldg(eps + c00) + w10 * __ldg(eps + c10) + w01 * __ldg(eps + c01) + w11 * __ldg(eps + c11);
-  T s = w00 * __ldg(sig + c00) + w10 * __ldg(sig + c10) + w01 * __ldg(sig + c01) + w11 * __ldg(sig + c11);
-  T ae = e * a.inv_dt;
-  cb = T(1) / (ae + T(0.5) * s);
-  ca = (ae - T(0.5) * s) * cb;
-}
-
-// (Da, Db) of an H edge from the two cells its dual edge crosses.
-template <typename T, typename ID>
-__device__ __forceinline__ void h_coef(const YeeArgs<T, ID> &a, ID c0, ID c1, T w0, T w1, T &da,
-                                       T &db) {
-  if (c0 == c1) {
-    da = __ldg(a.ctab + 2 * a.nmat + c0);
-    db = __ldg(a.ctab + 3 * a.nmat + c0);
-    return;
-  }
-  const T *mu = a.mtab + 2 * a.nmat, *sgm = a.mtab + 3 * a.nmat;
-  T m = w0 * __ldg(mu + c0) + w1 * __ldg(mu + c1);
-  T s = w0 * __ldg(sgm + c0) + w1 * __ldg(sgm + c1);
-  T am = m * a.inv_dt;
-  db = T(1) / (am + T(0.5) * s);
-  da = (am - T(0.5) * s) * db;
-}
 
 template <typename T, typename ID>
 struct YeeSmem {
@@ -274,6 +207,7 @@ static fdtd_status launch_yee_t(fdtd_grid *g, const void *u_row, void *y_row, in
                                 cudaStream_t s) {
   YeeArgs<T, ID> a;
   a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.kchunk = kchunk; a.nc = g->nc;
+  a.ntx = g->lists.ntx; a.nty = g->lists.nty;
   const T *in = g->fields[g->cur].as<T>();
   T *out = g->fields[g->cur ^ 1].as<T>();
   a.Ein = in; a.Hin = in + 3 * g->nc;
@@ -318,11 +252,23 @@ static fdtd_status launch_yee(fdtd_grid *g, const void *u_row, void *y_row, int 
                     : launch_yee_t<float, uint16_t, false>(g, u_row, y_row, kchunk, s);
 }
 
-int choose_kchunk(const fdtd_grid *g, int ntiles) {
-  const int target = 152 * 4;
-  int nchunks = std::max(1, (target + ntiles - 1) / ntiles);
-  nchunks = std::min(nchunks, std::max(1, g->nz / 4));
-  return (g->nz + nchunks - 1) / nchunks;
+// z-chunk length: enough CTAs to fill every SM, with the last wave as full as
+// possible (each chunk recomputes about two planes, so fewer chunks are
+// preferred when the wave efficiency is equal).
+int choose_kchunk(const fdtd_grid *g, int ntiles, int ctas_per_sm) {
+  const int cap = 152 * ctas_per_sm;
+  const int maxch = std::max(1, g->nz / 4);
+  double best = -1;
+  int best_k = g->nz;
+  for (int nch = 1; nch <= maxch; ++nch) {
+    const int kch = (g->nz + nch - 1) / nch;
+    const int used = (g->nz + kch - 1) / kch;
+    const long total = (long)ntiles * used;
+    const long waves = (total + cap - 1) / cap;
+    const double eff = (double)total / (double)(waves * cap) * (double)kch / (double)(kch + 2);
+    if (eff > best + 1e-9) { best = eff; best_k = kch; }
+  }
+  return best_k;
 }
 
 fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
@@ -332,17 +278,31 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
   FDTD_REQUIRE(nsteps == 0 || g->ports.empty() || u, "u is required when the grid has sources");
   FDTD_REQUIRE(nsteps == 0 || g->probes.empty() || y, "y is required when the grid has probes");
   FDTD_CHECK(ensure_coef_table(g, dt, s));
-  FDTD_CHECK(build_tile_lists(g, YTX, YTY, s));
+  int kind = g->kernel;
+  if (const char *e = getenv("FDTDMOR_YEE")) {  // override for measurements
+    const std::string v(e);
+    kind = v == "persist" ? FDTD_KERNEL_PERSIST : v == "split" ? FDTD_KERNEL_SPLIT
+         : v == "tma" ? FDTD_KERNEL_TMA : v == "fused" ? FDTD_KERNEL_FUSED : kind;
+  }
+  if (kind == FDTD_KERNEL_TMA && !yee_tma_eligible(g)) kind = FDTD_KERNEL_FUSED;
+  if (kind == FDTD_KERNEL_AUTO) kind = FDTD_KERNEL_SPLIT;
+  int ttx = YTX, tty = YTY;
+  if (kind == FDTD_KERNEL_TMA) yee_tma_tile(&ttx, &tty);
+  if (kind == FDTD_KERNEL_PERSIST || kind == FDTD_KERNEL_SPLIT) ttx = 32 * yee_split_vw(g);
+  FDTD_CHECK(build_tile_lists(g, ttx, tty, s));
   if (reset_fields) {
     FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)6 * g->nc * g->elem, s));
   }
   const int m = (int)g->ports.size(), p = (int)g->probes.size();
   if (p && nsteps) FDTD_CHECK_CUDA(cudaMemsetAsync(y, 0, (size_t)nsteps * p * g->elem, s));
-  const int kchunk = choose_kchunk(g, g->lists.ntx * g->lists.nty);
+  if (kind == FDTD_KERNEL_PERSIST) return run_yee_stream(g, nsteps, u, y, s);
+  const int kchunk = choose_kchunk(g, g->lists.ntx * g->lists.nty, kind == FDTD_KERNEL_TMA ? 3 : 4);
   for (int64_t n = 0; n < nsteps; ++n) {
     const char *ur = u ? static_cast<const char *>(u) + (size_t)n * m * g->elem : nullptr;
     char *yr = y ? static_cast<char *>(y) + (size_t)n * p * g->elem : nullptr;
-    FDTD_CHECK(launch_yee(g, ur, yr, kchunk, s));
+    if (kind == FDTD_KERNEL_SPLIT) FDTD_CHECK(launch_yee_split(g, ur, yr, s));
+    else if (kind == FDTD_KERNEL_TMA) FDTD_CHECK(launch_yee_tma(g, ur, yr, kchunk, s));
+    else FDTD_CHECK(launch_yee(g, ur, yr, kchunk, s));
     g->cur ^= 1;
   }
   return FDTD_OK;
@@ -353,6 +313,16 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
 using namespace fdtdmor;
 
 extern "C" {
+
+fdtd_status fdtd_grid_set_kernel(fdtd_grid *g, int kernel) {
+  FDTD_REQUIRE(g, "fdtd_grid_set_kernel: NULL grid");
+  FDTD_REQUIRE(kernel >= FDTD_KERNEL_AUTO && kernel <= FDTD_KERNEL_FUSED, "fdtd_grid_set_kernel: unknown kernel %d",
+               kernel);
+  FDTD_REQUIRE(kernel != FDTD_KERNEL_TMA || yee_tma_eligible(g),
+               "fdtd_grid_set_kernel: the TMA form needs nx a multiple of %d", g->id_bytes == 1 ? 16 : 8);
+  g->kernel = kernel;
+  return FDTD_OK;
+}
 
 fdtd_status fdtd_step(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
                       int reset_fields, fdtd_stream_t stream) {

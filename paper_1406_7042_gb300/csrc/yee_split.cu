@@ -1,0 +1,591 @@
+// A2: the Yee leap-frog of Eq. (matrix) as an E half step and an H half step.
+//
+// Two launch forms share the per-cell code (e_unit, h_unit):
+//  * split (large, HBM-bound grids): per leap-frog step one E launch over the
+//    whole grid, then one H launch, ping-ponging between the two field
+//    buffers.  Each thread owns one (i, j) column of a 32 x 8 tile and marches
+//    over a few planes in z, keeping the plane below (E) or above (H) in
+//    registers.
+//  * dataflow (yee_stream_kernel): one launch runs many steps in place; CTAs
+//    take (step, half, slab, tile) units in order and wait only for the slabs
+//    a unit depends on.  Yee updates are in-place safe: the E half reads E only
+//    at the edge it writes and H only at neighbours (H is not written in that
+//    half), and the H half the other way round.
+// Edge coefficients come from a per-cell map of "uniform neighbourhoods"
+// (emat): where the eight cells around a cell's E edges share one material the
+// kernel takes (Ca, Cb) from the material table, otherwise it averages the
+// edge material as in Eq. (matrix).  Sources are added by the CTA owning the
+// edge after its E update (block barrier, then an atomic on the global value);
+// probes are read in the H half from the final E^{n+1}.
+#include <algorithm>
+#include <cstdlib>
+#include <string>
+
+#include "common.cuh"
+#include "grid_internal.cuh"
+#include "yee_internal.cuh"
+
+namespace fdtdmor {
+
+constexpr int LTX = 32, LTY = 8;
+
+// Field loads: read-only path inside one split launch (no field is written
+// and read in the same launch), L2 (coherent across CTAs) in the dataflow
+// form, where the values were written by other CTAs earlier in the launch.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldf(const T *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+// Per cell: the material shared by the 8 cells around its E edges' dual faces
+// (i-1..i, j-1..j, k-1..k, inside the grid), or the sentinel ~0 when they differ.
+template <typename ID>
+__global__ void emat_kernel(const ID *__restrict__ mat, int nx, int ny, int nz, ID *__restrict__ out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)nx * ny;
+  if (n >= plane * nz) return;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / plane);
+  const ID m = mat[n];
+  bool uni = true;
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        if (i + di < 0 || j + dj < 0 || k + dk < 0) continue;
+        uni &= mat[n + dk * plane + dj * nx + di] == m;
+      }
+  out[n] = uni ? m : (ID)~(ID)0;
+}
+
+// VW consecutive values starting at p (p aligned to VW values): one 4-, 8- or
+// 16-byte load.
+template <int VW, bool COH, typename T>
+__device__ __forceinline__ void ldv(T (&r)[VW], const T *p) {
+  if constexpr (VW == 1) {
+    r[0] = ldf<COH>(p);
+  } else if constexpr (sizeof(T) == 4 && VW == 4) {
+    const float4 v = COH ? __ldcg(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  } else if constexpr (sizeof(T) == 4 && VW == 2) {
+    const float2 v = COH ? __ldcg(reinterpret_cast<const float2 *>(p)) : __ldg(reinterpret_cast<const float2 *>(p));
+    r[0] = v.x; r[1] = v.y;
+  } else {
+    static_assert(sizeof(T) == 8 && VW == 2, "unsupported vector width");
+    const double2 v = COH ? __ldcg(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+    r[0] = v.x; r[1] = v.y;
+  }
+}
+
+template <int VW, typename T>
+__device__ __forceinline__ void stv(T *p, const T (&r)[VW]) {
+  if constexpr (VW == 1) {
+    p[0] = r[0];
+  } else if constexpr (sizeof(T) == 4 && VW == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  } else if constexpr (sizeof(T) == 4 && VW == 2) {
+    *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
+  } else {
+    *reinterpret_cast<double2 *>(p) = make_double2(r[0], r[1]);
+  }
+}
+
+// VW material ids starting at p (aligned), in one load.
+template <int VW, typename ID>
+__device__ __forceinline__ void ldids(ID (&r)[VW], const ID *p) {
+  constexpr int B = VW * (int)sizeof(ID);
+  if constexpr (B == 1 || B == 2 && sizeof(ID) == 2) {
+    r[0] = __ldg(p);
+  } else if constexpr (B == 2) {
+    const unsigned short v = __ldg(reinterpret_cast<const unsigned short *>(p));
+    r[0] = (ID)(v & 0xff); r[1] = (ID)(v >> 8);
+  } else if constexpr (B == 4) {
+    const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+    if constexpr (sizeof(ID) == 1) { r[0] = (ID)(v & 0xff); r[1] = (ID)((v >> 8) & 0xff); r[2] = (ID)((v >> 16) & 0xff); r[3] = (ID)(v >> 24); }
+    else { r[0] = (ID)(v & 0xffff); r[1] = (ID)(v >> 16); }
+  } else {
+    static_assert(B == 8, "unsupported id width");
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+    r[0] = (ID)(v.x & 0xffff); r[1] = (ID)(v.x >> 16); r[2] = (ID)(v.y & 0xffff); r[3] = (ID)(v.y >> 16);
+  }
+}
+
+// E^{n+1} on planes [k0, k1) of tile (bx, by), which spans LTX * VW cells in
+// x: thread (tx, ty) owns cells i0 .. i0 + VW - 1 of row j and marches in z.
+// The x neighbour i0 - 1 comes from the lane to the left (a shuffle) or, for
+// lane 0, from one extra load.  All lanes of a warp run the loop, so lanes
+// past the end of a row (whose loads read as zero) still feed the shuffles.
+// In place when a.Eout == a.Ein: the only E value read is the one written by
+// the same thread, and the store depends on it.
+template <typename T, typename ID, bool COH, int VW>
+__device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__restrict__ emat, int bx, int by,
+                                       int k0, int k1) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * LTX + tx;
+  const int i0 = (bx * LTX + tx) * VW, j = by * LTY + ty;
+  const int nx = a.nx, ny = a.ny, ntot = nx + ny + a.nz;
+  const int64_t nc = a.nc, plane = (int64_t)nx * ny;
+  auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+  if (j < ny) {  // warp-uniform
+    const bool live = i0 < nx;
+    const T ryd = ax(AX_RDD, nx + j), wyl = ax(AX_WLO, nx + j), wyh = ax(AX_WHI, nx + j);
+    T rxd[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) rxd[e] = live ? ax(AX_RDD, i0 + e) : T(0);
+    const T *Hx = a.Hin, *Hy = a.Hin + nc, *Hz = a.Hin + 2 * nc;
+    const ID *M = a.mat;
+    const ID none = (ID)~(ID)0;
+    int64_t n = k0 * plane + (int64_t)j * nx + i0;
+    T hx_km[VW], hy_km[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) hx_km[e] = hy_km[e] = T(0);
+    if (live && k0 > 0) {
+      ldv<VW, COH>(hx_km, Hx + n - plane);
+      ldv<VW, COH>(hy_km, Hy + n - plane);
+    }
+    for (int k = k0; k < k1; ++k, n += plane) {
+      T hx[VW], hy[VW], hz[VW], hx_jm[VW], hz_jm[VW], ex[VW], ey[VW], ez[VW];
+      ID mu[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) hx[e] = hy[e] = hz[e] = hx_jm[e] = hz_jm[e] = ex[e] = ey[e] = ez[e] = T(0);
+      T hy_l = T(0), hz_l = T(0);  // Hy, Hz at i0 - 1 for lane 0
+      if (live) {
+        ldv<VW, COH>(hx, Hx + n);
+        ldv<VW, COH>(hy, Hy + n);
+        ldv<VW, COH>(hz, Hz + n);
+        if (j > 0) {
+          ldv<VW, COH>(hx_jm, Hx + n - nx);
+          ldv<VW, COH>(hz_jm, Hz + n - nx);
+        }
+        ldv<VW, COH>(ex, a.Ein + n);
+        ldv<VW, COH>(ey, a.Ein + nc + n);
+        ldv<VW, COH>(ez, a.Ein + 2 * nc + n);
+        ldids<VW>(mu, emat + n);
+        if (tx == 0 && i0 > 0) {
+          hy_l = ldf<COH>(Hy + n - 1);
+          hz_l = ldf<COH>(Hz + n - 1);
+        }
+      }
+      const T hy_s = __shfl_up_sync(0xffffffffu, hy[VW - 1], 1), hz_s = __shfl_up_sync(0xffffffffu, hz[VW - 1], 1);
+      if (tx > 0) { hy_l = hy_s; hz_l = hz_s; }
+      if (live) {
+        const T rzd = ax(AX_RDD, nx + ny + k);
+        T ox[VW], oy[VW], oz[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          const int i = i0 + e;
+          const T hy_im = e == 0 ? hy_l : hy[e - 1], hz_im = e == 0 ? hz_l : hz[e - 1];
+          T cax, cbx, cay, cby, caz, cbz;
+          if (mu[e] != none) {
+            cax = cay = caz = __ldg(a.ctab + mu[e]);
+            cbx = cby = cbz = __ldg(a.ctab + a.nmat + mu[e]);
+          } else {
+            const int64_t c = n + e;
+            const T wxl = ax(AX_WLO, i), wxh = ax(AX_WHI, i);
+            const T wzl = ax(AX_WLO, nx + ny + k), wzh = ax(AX_WHI, nx + ny + k);
+            const ID m = M[c];
+            const ID m_i = i > 0 ? M[c - 1] : m, m_j = j > 0 ? M[c - nx] : m, m_k = k > 0 ? M[c - plane] : m;
+            const ID m_ij = (i > 0 && j > 0) ? M[c - 1 - nx] : m, m_ik = (i > 0 && k > 0) ? M[c - 1 - plane] : m;
+            const ID m_jk = (j > 0 && k > 0) ? M[c - nx - plane] : m;
+            e_coef(a, m_jk, m_k, m_j, m, wyl, wyh, wzl, wzh, cax, cbx);
+            e_coef(a, m_ik, m_k, m_i, m, wxl, wxh, wzl, wzh, cay, cby);
+            e_coef(a, m_ij, m_j, m_i, m, wxl, wxh, wyl, wyh, caz, cbz);
+          }
+          if (j == 0 || k == 0) cax = cbx = T(0);
+          if (i == 0 || k == 0) cay = cby = T(0);
+          if (i == 0 || j == 0) caz = cbz = T(0);
+          ox[e] = cax * ex[e] + cbx * ((hz[e] - hz_jm[e]) * ryd - (hy[e] - hy_km[e]) * rzd);
+          oy[e] = cay * ey[e] + cby * ((hx[e] - hx_km[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
+          oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
+        }
+        stv<VW>(a.Eout + n, ox);
+        stv<VW>(a.Eout + nc + n, oy);
+        stv<VW>(a.Eout + 2 * nc + n, oz);
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        hx_km[e] = hx[e];
+        hy_km[e] = hy[e];
+      }
+    }
+  }
+  // sources of this tile on these planes: E -= Cb w u
+  const int tile = by * a.ntx + bx;
+  const int s0 = a.src_ptr[tile], s1 = a.src_ptr[tile + 1];
+  if (s1 > s0) {
+    __syncthreads();
+    for (int q = s0 + tid; q < s1; q += LTX * LTY) {
+      const PortEntry pe = a.src[q];
+      if (pe.k < k0 || pe.k >= k1 || pe.lx >= LTX * VW || pe.ly >= LTY) continue;
+      const int si = bx * LTX * VW + pe.lx, sj = by * LTY + pe.ly, k = pe.k;
+      if (si >= nx || sj >= ny) continue;
+      const int64_t n = k * plane + (int64_t)sj * nx + si;
+      const ID *M = a.mat;
+      T ca, cb = 0;
+      const T wzl = ax(AX_WLO, nx + ny + k), wzh = ax(AX_WHI, nx + ny + k);
+      if (pe.comp == 0 && sj > 0 && k > 0)
+        e_coef(a, M[n - nx - plane], M[n - plane], M[n - nx], M[n], ax(AX_WLO, nx + sj), ax(AX_WHI, nx + sj), wzl, wzh, ca, cb);
+      else if (pe.comp == 1 && si > 0 && k > 0)
+        e_coef(a, M[n - 1 - plane], M[n - plane], M[n - 1], M[n], ax(AX_WLO, si), ax(AX_WHI, si), wzl, wzh, ca, cb);
+      else if (pe.comp == 2 && si > 0 && sj > 0)
+        e_coef(a, M[n - 1 - nx], M[n - nx], M[n - 1], M[n], ax(AX_WLO, si), ax(AX_WHI, si), ax(AX_WLO, nx + sj),
+               ax(AX_WHI, nx + sj), ca, cb);
+      atomicAdd(&a.Eout[pe.comp * nc + n], -cb * (T)pe.w * a.u[pe.port]);
+    }
+  }
+}
+
+// H^{n+3/2} on planes [k0, k1) of tile (bx, by), from E^{n+1} in a.Eout; the
+// x neighbour i0 + VW comes from the lane to the right or, for lane 31, from
+// one extra load.  In place when a.Hout == a.Hin (as in e_unit).
+template <typename T, typename ID, bool HOMOG_H, bool COH, int VW>
+__device__ __forceinline__ void h_unit(const YeeArgs<T, ID> &a, int bx, int by, int k0, int k1) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * LTX + tx;
+  const int i0 = (bx * LTX + tx) * VW, j = by * LTY + ty;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
+  const int64_t nc = a.nc, plane = (int64_t)nx * ny;
+  auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+  const T *Ex = a.Eout, *Ey = a.Eout + nc, *Ez = a.Eout + 2 * nc;  // E^{n+1}
+  if (j < ny) {  // warp-uniform
+    const bool live = i0 < nx;
+    const T rdy = ax(AX_RD, nx + j);
+    T rdx[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) rdx[e] = live ? ax(AX_RD, i0 + e) : T(0);
+    const T da0 = __ldg(a.ctab + 2 * a.nmat), db0 = __ldg(a.ctab + 3 * a.nmat);
+    int64_t n = k0 * plane + (int64_t)j * nx + i0;
+    T ex[VW], ey[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) ex[e] = ey[e] = T(0);
+    if (live) {
+      ldv<VW, COH>(ex, Ex + n);
+      ldv<VW, COH>(ey, Ey + n);
+    }
+    for (int k = k0; k < k1; ++k, n += plane) {
+      T ez[VW], ex_kp[VW], ey_kp[VW], ex_jp[VW], ez_jp[VW], h0[VW], h1[VW], h2[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) ez[e] = ex_kp[e] = ey_kp[e] = ex_jp[e] = ez_jp[e] = h0[e] = h1[e] = h2[e] = T(0);
+      T ey_r = T(0), ez_r = T(0);  // Ey, Ez at i0 + VW for lane 31
+      if (live) {
+        ldv<VW, COH>(ez, Ez + n);
+        if (k + 1 < nz) {
+          ldv<VW, COH>(ex_kp, Ex + n + plane);
+          ldv<VW, COH>(ey_kp, Ey + n + plane);
+        }
+        if (j + 1 < ny) {
+          ldv<VW, COH>(ex_jp, Ex + n + nx);
+          ldv<VW, COH>(ez_jp, Ez + n + nx);
+        }
+        ldv<VW, COH>(h0, a.Hin + n);
+        ldv<VW, COH>(h1, a.Hin + nc + n);
+        ldv<VW, COH>(h2, a.Hin + 2 * nc + n);
+        if (tx == LTX - 1 && i0 + VW < nx) {
+          ey_r = ldf<COH>(Ey + n + VW);
+          ez_r = ldf<COH>(Ez + n + VW);
+        }
+      }
+      const T ey_s = __shfl_down_sync(0xffffffffu, ey[0], 1), ez_s = __shfl_down_sync(0xffffffffu, ez[0], 1);
+      if (tx < LTX - 1) { ey_r = ey_s; ez_r = ez_s; }
+      if (live) {
+        const T rdz = ax(AX_RD, nx + ny + k);
+        T ox[VW], oy[VW], oz[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          const int i = i0 + e;
+          const T ey_ip = e == VW - 1 ? ey_r : ey[e + 1], ez_ip = e == VW - 1 ? ez_r : ez[e + 1];
+          T da[3] = {da0, da0, da0}, db[3] = {db0, db0, db0};
+          if (!HOMOG_H) {
+            const ID *M = a.mat;
+            const int64_t c = n + e;
+            const ID m = M[c];
+            if (i > 0) h_coef(a, M[c - 1], m, ax(AX_WLO, i), ax(AX_WHI, i), da[0], db[0]);
+            if (j > 0) h_coef(a, M[c - nx], m, ax(AX_WLO, nx + j), ax(AX_WHI, nx + j), da[1], db[1]);
+            if (k > 0) h_coef(a, M[c - plane], m, ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), da[2], db[2]);
+          }
+          const T hx = da[0] * h0[e] - db[0] * ((ez_jp[e] - ez[e]) * rdy - (ey_kp[e] - ey[e]) * rdz);
+          const T hy = da[1] * h1[e] - db[1] * ((ex_kp[e] - ex[e]) * rdz - (ez_ip - ez[e]) * rdx[e]);
+          const T hz = da[2] * h2[e] - db[2] * ((ey_ip - ey[e]) * rdx[e] - (ex_jp[e] - ex[e]) * rdy);
+          ox[e] = i == 0 ? T(0) : hx;
+          oy[e] = j == 0 ? T(0) : hy;
+          oz[e] = k == 0 ? T(0) : hz;
+        }
+        stv<VW>(a.Hout + n, ox);
+        stv<VW>(a.Hout + nc + n, oy);
+        stv<VW>(a.Hout + 2 * nc + n, oz);
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        ex[e] = ex_kp[e];
+        ey[e] = ey_kp[e];
+      }
+    }
+  }
+  // probes of this tile on these planes read the final E^{n+1}
+  const int tile = by * a.ntx + bx;
+  const int p0 = a.prb_ptr[tile], p1 = a.prb_ptr[tile + 1];
+  for (int q = p0 + tid; q < p1; q += LTX * LTY) {
+    const PortEntry pe = a.prb[q];
+    if (pe.k < k0 || pe.k >= k1) continue;
+    const int si = bx * LTX * VW + pe.lx, sj = by * LTY + pe.ly;
+    if (si >= nx || sj >= ny) continue;
+    atomicAdd(&a.y[pe.port], (T)pe.w * ldf<COH>(a.Eout + pe.comp * nc + pe.k * plane + (int64_t)sj * nx + si));
+  }
+}
+
+template <typename T, typename ID, int VW>
+__global__ void __launch_bounds__(LTX *LTY) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+  const int k0 = blockIdx.z * lz;
+  e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+}
+
+template <typename T, typename ID, bool HOMOG_H, int VW>
+__global__ void __launch_bounds__(LTX *LTY) yee_h_kernel(YeeArgs<T, ID> a, int lz) {
+  const int k0 = blockIdx.z * lz;
+  h_unit<T, ID, HOMOG_H, false, VW>(a, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+}
+
+// Bounded wait until *c >= target (acquire).  Gives up after about a second,
+// or at once when another CTA has given up, setting *err; returns false then.
+__device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, unsigned *err) {
+  for (long spins = 0;; ++spins) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= target) return true;
+    if ((spins & 31) == 0) {
+      unsigned e;
+      asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+      if (e) return false;
+    }
+    if (spins > (1l << 24)) {
+      atomicOr(err, 2u);
+      return false;
+    }
+    if (spins > 16) __nanosleep(64);
+  }
+}
+
+// Dataflow form: nsteps leap-frog steps in place on (E, H) = a.Ein = a.Eout,
+// a.Hin = a.Hout, without grid-wide barriers.
+//
+// The grid is cut into nslab z slabs of lz planes; a work unit is one tile of
+// one slab in one half step.  Per step the units are ticketed in the order
+//   E(0), E(1), H(0), E(2), H(1), ..., E(S-1), H(S-2), H(S-1)
+// (each slab's units together), and CTAs take tickets from an atomic counter.
+// cnt[1 + s] counts finished E units of slab s and cnt[1 + S + s] finished H
+// units, cumulatively over the steps of the launch.  Dependencies, which are
+// also the in-place hazards:
+//   E(s) of step n needs H(s), H(s-1) of step n-1   (H^{n+1/2} at k and k-1),
+//   H(s) of step n needs E(s), E(s+1) of step n     (E^{n+1} at k and k+1).
+// Every dependency of a ticket has a smaller ticket, held by a running CTA, so
+// the smallest unfinished ticket can always proceed: no co-residency is needed
+// and the kernel cannot deadlock.  With the units of neighbouring slabs in
+// flight together, E^{n+1} and H^{n+1/2} of a slab are still in L2 when its H
+// units run, so DRAM sees each field read once and written once per step.
+template <typename T, typename ID, bool HOMOG_H, int VW>
+__global__ void __launch_bounds__(LTX *LTY, 2) yee_stream_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
+                                                              int nslab, int64_t nsteps, const T *u, int m, T *y,
+                                                              int p, unsigned *cnt, unsigned *err) {
+  __shared__ long long s_ticket;
+  __shared__ int s_ok;
+  const int tid = threadIdx.y * LTX + threadIdx.x;
+  const int ntile = a.ntx * a.nty;
+  const long long per_step = 2ll * nslab * ntile;
+  const long long total = per_step * nsteps;
+  unsigned *ticket = cnt, *doneE = cnt + 1, *doneH = cnt + 1 + nslab;
+  for (;;) {
+    if (tid == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long t = s_ticket;
+    if (t >= total) break;
+    const int n = (int)(t / per_step);
+    const long long r = t - n * per_step;
+    const int b = (int)(r / ntile), tile = (int)(r - (long long)b * ntile);
+    // block b of the step: 0 -> E(0); odd b < 2S-1 -> E((b+1)/2); even b -> H(b/2-1); 2S-1 -> H(S-1)
+    bool is_e;
+    int sl;
+    if (b == 0) { is_e = true; sl = 0; }
+    else if (b == 2 * nslab - 1) { is_e = false; sl = nslab - 1; }
+    else if (b & 1) { is_e = true; sl = (b + 1) / 2; }
+    else { is_e = false; sl = b / 2 - 1; }
+    if (tid == 0) {
+      bool ok = true;
+      if (is_e) {
+        const unsigned need = (unsigned)n * ntile;
+        ok = wait_count(doneH + sl, need, err) && (sl == 0 || wait_count(doneH + sl - 1, need, err));
+      } else {
+        const unsigned need = (unsigned)(n + 1) * ntile;
+        ok = wait_count(doneE + sl, need, err) && (sl + 1 == nslab || wait_count(doneE + sl + 1, need, err));
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int k0 = sl * lz, k1 = min(a.nz, k0 + lz);
+    const int bx = tile % a.ntx, by = tile / a.ntx;
+    if (is_e) {
+      a.u = u ? u + (int64_t)n * m : nullptr;
+      e_unit<T, ID, true, VW>(a, emat, bx, by, k0, k1);
+    } else {
+      a.y = y ? y + (int64_t)n * p : nullptr;
+      h_unit<T, ID, HOMOG_H, true, VW>(a, bx, by, k0, k1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(is_e ? doneE + sl : doneH + sl, 1u);
+    }
+  }
+}
+
+// Cells per thread along x: the widest of 16, 8 bytes whose vectors divide
+// the rows (every vector load is then aligned) and whose 32-lane tile is not
+// wider than a row, else 1.
+int yee_split_vw(const fdtd_grid *g) {
+  if (getenv("FDTDMOR_NO_VEC")) return 1;
+  for (int v = 16 / (int)g->elem; v >= 2; v /= 2)
+    if (g->nx % v == 0 && 32 * v <= g->nx) return v;
+  return 1;
+}
+
+static int env_int(const char *name, int dflt) {
+  const char *e = getenv(name);
+  return e ? std::max(1, atoi(e)) : dflt;
+}
+
+static int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <typename T, typename ID>
+static YeeArgs<T, ID> split_args(fdtd_grid *g) {
+  YeeArgs<T, ID> a;
+  a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.kchunk = 0; a.nc = g->nc;
+  a.ntx = g->lists.ntx; a.nty = g->lists.nty;
+  const T *in = g->fields[g->cur].as<T>();
+  T *out = g->fields[g->cur ^ 1].as<T>();
+  a.Ein = in; a.Hin = in + 3 * g->nc;
+  a.Eout = out; a.Hout = out + 3 * g->nc;
+  a.mat = g->mat.as<ID>();
+  a.ax = g->axis.as<T>();
+  a.mtab = g->mtab.as<T>();
+  a.ctab = g->ctab.as<T>();
+  a.nmat = g->nmat;
+  a.inv_dt = (T)(1.0 / g->ctab_dt);
+  a.src_ptr = g->lists.src_ptr.as<int32_t>();
+  a.src = g->lists.src.as<PortEntry>();
+  a.u = nullptr;
+  a.prb_ptr = g->lists.prb_ptr.as<int32_t>();
+  a.prb = g->lists.prb.as<PortEntry>();
+  a.y = nullptr;
+  return a;
+}
+
+template <typename ID>
+static fdtd_status ensure_emat(fdtd_grid *g, cudaStream_t s) {
+  if (g->emat_ready) return FDTD_OK;
+  FDTD_CHECK(g->emat.alloc((size_t)g->nc * sizeof(ID), s));
+  emat_kernel<ID><<<(int)((g->nc + 255) / 256), 256, 0, s>>>(g->mat.as<ID>(), g->nx, g->ny, g->nz, g->emat.as<ID>());
+  FDTD_CHECK(after_launch("emat_kernel"));
+  g->emat_ready = true;
+  return FDTD_OK;
+}
+
+// One step as an E launch and an H launch, out of place (fields[cur] ->
+// fields[cur ^ 1]).
+template <typename T, typename ID, bool HH, int VW>
+static fdtd_status launch_split_v(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  FDTD_CHECK(ensure_emat<ID>(g, s));
+  YeeArgs<T, ID> a = split_args<T, ID>(g);
+  a.u = static_cast<const T *>(u_row);
+  a.y = static_cast<T *>(y_row);
+  // z planes per thread: 4 once the grid has work for several waves, else 1
+  const int64_t cols = (int64_t)g->lists.ntx * g->lists.nty * LTX * LTY;
+  const int lz = std::min(g->nz, env_int("FDTDMOR_LZ", cols * g->nz >= 4ll * 2048 * device_sms() ? 4 : 1));
+  const dim3 grid(g->lists.ntx, g->lists.nty, (g->nz + lz - 1) / lz), block(LTX, LTY);
+  yee_e_kernel<T, ID, VW><<<grid, block, 0, s>>>(a, g->emat.as<ID>(), lz);
+  FDTD_CHECK(after_launch("yee_e_kernel"));
+  yee_h_kernel<T, ID, HH, VW><<<grid, block, 0, s>>>(a, lz);
+  return after_launch("yee_h_kernel");
+}
+
+template <typename T, typename ID, bool HH>
+static fdtd_status launch_split_t(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  const int vw = yee_split_vw(g);
+  if (sizeof(T) == 4 && vw == 4) return launch_split_v<T, ID, HH, 16 / sizeof(T)>(g, u_row, y_row, s);
+  if (vw == 2) return launch_split_v<T, ID, HH, 2>(g, u_row, y_row, s);
+  return launch_split_v<T, ID, HH, 1>(g, u_row, y_row, s);
+}
+
+// nsteps steps in place on fields[cur], as launches of the dataflow kernel of
+// up to kStreamChunk steps each (the counters restart with every launch).
+constexpr int64_t kStreamChunk = 8192;
+
+template <typename T, typename ID, bool HH, int VW>
+static fdtd_status run_stream_v(fdtd_grid *g, int64_t nsteps, const void *u, void *y, cudaStream_t s) {
+  FDTD_CHECK(ensure_emat<ID>(g, s));
+  YeeArgs<T, ID> a = split_args<T, ID>(g);
+  a.Eout = const_cast<T *>(a.Ein);
+  a.Hout = const_cast<T *>(a.Hin);
+  auto kern = yee_stream_kernel<T, ID, HH, VW>;
+  int occ = 0;
+  FDTD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, LTX * LTY, 0));
+  FDTD_REQUIRE(occ >= 1, "yee dataflow kernel: no resident CTA per SM");
+  const int cap = occ * device_sms();
+  const int ntile = g->lists.ntx * g->lists.nty;
+  // one-plane slabs while a step has few units per resident CTA, else four
+  int lz = (int64_t)ntile * g->nz <= 4ll * cap ? 1 : 4;
+  lz = std::min(g->nz, env_int("FDTDMOR_LZ", lz));
+  const int nslab = (g->nz + lz - 1) / lz;
+  const int64_t per_step = 2ll * nslab * ntile;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(kStreamChunk, (int64_t(1) << 31) / per_step));
+  FDTD_REQUIRE(per_step < (int64_t(1) << 31), "yee dataflow kernel: grid too large for 32-bit tickets");
+  const size_t ncnt = 1 + 2 * (size_t)nslab;
+  FDTD_CHECK(g->gsync.alloc(ncnt * sizeof(unsigned), s));
+  const int nblk = (int)std::min<int64_t>(cap, per_step * std::min(chunk, nsteps));
+  const int m = (int)g->ports.size(), p = (int)g->probes.size();
+  const ID *emat = g->emat.as<ID>();
+  unsigned *cnt = g->gsync.as<unsigned>(), *err = g->errflag.as<unsigned>();
+  for (int64_t n0 = 0; n0 < nsteps; n0 += chunk) {
+    const int64_t c = std::min(chunk, nsteps - n0);
+    const T *uc = u ? static_cast<const T *>(u) + n0 * m : nullptr;
+    T *yc = y ? static_cast<T *>(y) + n0 * p : nullptr;
+    FDTD_CHECK_CUDA(cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), s));
+    kern<<<nblk, dim3(LTX, LTY), 0, s>>>(a, emat, lz, nslab, c, uc, m, yc, p, cnt, err);
+    FDTD_CHECK(after_launch("yee_stream_kernel"));
+  }
+  return FDTD_OK;
+}
+
+template <typename T, typename ID, bool HH>
+static fdtd_status run_stream_t(fdtd_grid *g, int64_t nsteps, const void *u, void *y, cudaStream_t s) {
+  const int vw = yee_split_vw(g);
+  if (sizeof(T) == 4 && vw == 4) return run_stream_v<T, ID, HH, 16 / sizeof(T)>(g, nsteps, u, y, s);
+  if (vw == 2) return run_stream_v<T, ID, HH, 2>(g, nsteps, u, y, s);
+  return run_stream_v<T, ID, HH, 1>(g, nsteps, u, y, s);
+}
+
+#define YEE_DISPATCH(FN, ...)                                                                         \
+  do {                                                                                               \
+    if (g->prec == FDTD_F64) {                                                                       \
+      if (g->id_bytes == 1)                                                                          \
+        return g->homog_h ? FN<double, uint8_t, true>(__VA_ARGS__) : FN<double, uint8_t, false>(__VA_ARGS__); \
+      return g->homog_h ? FN<double, uint16_t, true>(__VA_ARGS__) : FN<double, uint16_t, false>(__VA_ARGS__); \
+    }                                                                                                \
+    if (g->id_bytes == 1)                                                                            \
+      return g->homog_h ? FN<float, uint8_t, true>(__VA_ARGS__) : FN<float, uint8_t, false>(__VA_ARGS__);     \
+    return g->homog_h ? FN<float, uint16_t, true>(__VA_ARGS__) : FN<float, uint16_t, false>(__VA_ARGS__);     \
+  } while (0)
+
+fdtd_status launch_yee_split(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  YEE_DISPATCH(launch_split_t, g, u_row, y_row, s);
+}
+
+fdtd_status run_yee_stream(fdtd_grid *g, int64_t nsteps, const void *u, void *y, cudaStream_t s) {
+  YEE_DISPATCH(run_stream_t, g, nsteps, u, y, s);
+}
+
+}  // namespace fdtdmor

@@ -97,6 +97,8 @@ _SIGS = [
     ("fdtd_fields_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_launch_count", C.c_int64, [C.c_int]),
     ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("fdtd_grid_set_kernel", C.c_int, [C.c_void_p, C.c_int]),
     ("mor_opts_default", C.c_int, [C.POINTER(MorOpts)]),
     ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_basis_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -249,6 +251,14 @@ class Grid:
         except Exception:
             pass
 
+    def check(self, stream=None):
+        """Raise if a bounded device wait of an earlier step gave up."""
+        check(lib().fdtd_check(self.h, _stream_ptr(stream)))
+
+    def set_kernel(self, kernel: str):
+        """Leap-frog kernel form: 'auto', 'persist', 'split', 'tma' or 'fused'."""
+        check(lib().fdtd_grid_set_kernel(self.h, KERNELS[kernel]))
+
     def cfl_dt(self) -> float:
         return float(lib().fdtd_cfl_dt(self.h))
 
@@ -290,6 +300,8 @@ class Grid:
         f = f.contiguous()
         check(lib().fdtd_fields_set(self.h, _dptr(f), _stream_ptr(stream)))
 
+
+KERNELS = {"auto": 0, "persist": 1, "split": 2, "tma": 3, "fused": 4}
 
 MODEL_FIELDS = {"De": 0, "Dse": 1, "Dm": 2, "Dsm": 3, "K": 4, "Kp": 5, "BE": 6, "CE": 7, "sigma": 8}
 

@@ -18,8 +18,9 @@ TOL_F32_PROBE = 2e-4
 TOL_F64 = 1e-9
 
 
-def _run_gpu(grid, prec, dt, u, reset=True):
+def _run_gpu(grid, prec, dt, u, reset=True, kernel="auto"):
     g = F.Grid(grid, prec)
+    g.set_kernel(kernel)
     ut = torch.tensor(u, dtype=g.dtype, device="cuda")
     y = g.step(dt, ut, reset=reset)
     f = g.fields()
@@ -43,13 +44,21 @@ def test_cfl_matches_oracle():
         assert abs(g.cfl_dt() - yee.cfl_dt(grid)) <= 1e-15 * yee.cfl_dt(grid)
 
 
+KERNEL_CASES = [("persist", 41), ("split", 41), ("fused", 41), ("persist", 48), ("split", 48), ("tma", 48)]
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("many", [False, True])
-def test_ragged_graded_lossy_parity(prec, many):
-    grid = ragged_grid(many_materials=many)
+@pytest.mark.parametrize("kernel,nx", KERNEL_CASES)
+def test_ragged_graded_lossy_parity(prec, many, kernel, nx):
+    """Every kernel form on a ragged graded lossy grid.  nx = 41: x rows not
+    a multiple of the 32-wide tiles; nx = 48: rows 16-byte aligned, as the
+    TMA form needs (uint8 ids with few materials, uint16 with many)."""
+    grid = ragged_grid(nx=nx, many_materials=many)
     dt = 0.95 * yee.cfl_dt(grid)
     u = drive(grid, dt, 160)
-    g, yg, fg = _run_gpu(grid, prec, dt, u)
+    g, yg, fg = _run_gpu(grid, prec, dt, u, kernel=kernel)
+    g.check()
     s, yo, fo = _run_oracle(grid, dt, u)
     if prec == "f64":
         assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
@@ -74,11 +83,13 @@ def test_config1_f64_full_run():
     assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
 
 
-def test_state_continues_across_calls_and_host_variant():
+@pytest.mark.parametrize("kernel", ["persist", "split", "fused"])
+def test_state_continues_across_calls_and_host_variant(kernel):
     grid = ragged_grid(seed=7)
     dt = 0.9 * yee.cfl_dt(grid)
     u = drive(grid, dt, 90)
     g = F.Grid(grid, "f32")
+    g.set_kernel(kernel)
     ut = torch.tensor(u, dtype=torch.float32, device="cuda")
     y1 = g.step(dt, ut[:40], reset=True)
     y2 = g.step(dt, ut[40:], reset=False)
@@ -94,6 +105,29 @@ def test_state_continues_across_calls_and_host_variant():
     yh = torch.empty((90, g.p), dtype=torch.float32).pin_memory()
     g.step_host(dt, uh, yh, reset=True)
     assert np.allclose(yh.numpy(), yref, rtol=1e-6, atol=1e-7 * np.abs(yref).max())
+    g.check()
+
+
+def test_kernel_forms_agree_and_persistent_chunks():
+    """8200 steps cross the persistent form's 8192-step launch boundary; the
+    FP64 result must equal the oracle's and the other forms' results."""
+    grid = ragged_grid(nx=12, ny=10, nz=9, seed=11)
+    dt = 0.97 * yee.cfl_dt(grid)
+    u = drive(grid, dt, 8200)
+    _, yo, fo = _run_oracle(grid, dt, u)
+    for kernel in ("persist", "split", "fused"):
+        g, yg, fg = _run_gpu(grid, "f64", dt, u, kernel=kernel)
+        g.check()
+        assert np.max(np.abs(fg - fo)) <= 1e-8 * np.abs(fo).max(), kernel
+        assert np.max(np.abs(yg - yo)) <= 1e-8 * np.abs(yo).max(), kernel
+
+
+def test_set_kernel_rejects_bad_values():
+    g = F.Grid(ragged_grid(nx=41), "f32")
+    with pytest.raises(F.FdtdError):
+        g.set_kernel("tma")              # 41 is not a multiple of 16
+    with pytest.raises(F.FdtdError):
+        F.check(F.lib().fdtd_grid_set_kernel(g.h, 9))
 
 
 def test_degenerate_grids_and_empty_ports():
