@@ -39,6 +39,7 @@ fdtd_status cuda_fail(cudaError_t e, const char *what);
 
 // After a kernel launch: count it and surface launch-configuration errors.
 fdtd_status after_launch(const char *name);
+void add_launches(int64_t n);  // kernel launches made by a graph replay
 
 // ------------------------------------------------------------ memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
@@ -116,6 +117,12 @@ struct fdtd_grid {
   double ctab_dt = -1;
   fdtdmor::TileLists lists;
   fdtdmor::DevBuf u_stage, y_stage;  // device staging for fdtd_step_host
+  // captured chunks of leap-frog steps (by parity of cur at their start) and
+  // what they were captured for; fixed staging rows for their u and y
+  cudaGraphExec_t ygraph[2] = {nullptr, nullptr};
+  uint64_t ygraph_key[2][8] = {};
+  cudaStream_t cap_stream = nullptr;
+  fdtdmor::DevBuf u_graph, y_graph;
   fdtdmor::DevBuf gsync;        // ticket and per-slab completion counters of the dataflow kernel
   int kernel = 0;               // fdtd_kernel chosen by fdtd_grid_set_kernel (0 = automatic)
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0

@@ -304,6 +304,11 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->uflag.release(s);
   g->emat.release(s);
   g->gsync.release(s);
+  g->u_graph.release(s);
+  g->y_graph.release(s);
+  for (auto &x : g->ygraph)
+    if (x) cudaGraphExecDestroy(x);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   cudaStreamSynchronize(s);
   delete g;
   return FDTD_OK;

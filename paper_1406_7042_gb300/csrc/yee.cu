@@ -15,6 +15,7 @@
 // cells (the non-uniform, inhomogeneous reading of Sec. II-A).
 #include <algorithm>
 
+#include <cstring>
 #include <string>
 
 #include "common.cuh"
@@ -271,6 +272,66 @@ int choose_kchunk(const fdtd_grid *g, int ntiles, int ctas_per_sm) {
   return best_k;
 }
 
+// Leap-frog steps per captured graph (even, so a replay leaves cur unchanged).
+constexpr int kGraphSteps = 32;
+
+// The graph of kGraphSteps steps starting from parity g->cur, captured on a
+// private stream the first time and whenever what it baked in has changed.
+static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s, cudaGraphExec_t *out) {
+  const int m = (int)g->ports.size(), p = (int)g->probes.size();
+  if (m) FDTD_CHECK(g->u_graph.alloc((size_t)kGraphSteps * m * g->elem, s));
+  if (p) FDTD_CHECK(g->y_graph.alloc((size_t)kGraphSteps * p * g->elem, s));
+  double dt = g->ctab_dt;
+  uint64_t key[8] = {(uint64_t)kind, (uint64_t)kchunk ^ ((uint64_t)(uintptr_t)g->ctab.ptr << 8), 0,
+                     (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
+                     (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr, (uint64_t)(uintptr_t)g->emat.ptr,
+                     (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),
+                     (uint64_t)g->lists.tx << 32 | (uint64_t)g->lists.ty};
+  memcpy(&key[2], &dt, sizeof(dt));
+  const int c = g->cur;
+  if (g->ygraph[c] && memcmp(key, g->ygraph_key[c], sizeof(key)) == 0) {
+    *out = g->ygraph[c];
+    return FDTD_OK;
+  }
+  if (g->ygraph[c]) {
+    cudaGraphExecDestroy(g->ygraph[c]);
+    g->ygraph[c] = nullptr;
+  }
+  if (!g->cap_stream) FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = g->cap_stream;
+  const int64_t launches_before = fdtd_launch_count(0);
+  FDTD_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  fdtd_status st = FDTD_OK;
+  if (p && cudaMemsetAsync(g->y_graph.ptr, 0, (size_t)kGraphSteps * p * g->elem, cs) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "graph memset");
+  for (int n = 0; n < kGraphSteps && st == FDTD_OK; ++n) {
+    const char *ur = m ? static_cast<const char *>(g->u_graph.ptr) + (size_t)n * m * g->elem : nullptr;
+    char *yr = p ? static_cast<char *>(g->y_graph.ptr) + (size_t)n * p * g->elem : nullptr;
+    if (kind == FDTD_KERNEL_SPLIT) st = launch_yee_split(g, ur, yr, cs);
+    else if (kind == FDTD_KERNEL_TMA) st = launch_yee_tma(g, ur, yr, kchunk, cs);
+    else st = launch_yee(g, ur, yr, kchunk, cs);
+    g->cur ^= 1;
+  }
+  g->cur = c;
+  add_launches(launches_before - fdtd_launch_count(0));  // captured, not launched
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (st != FDTD_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  const cudaError_t e2 = cudaGraphInstantiate(&g->ygraph[c], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    g->ygraph[c] = nullptr;
+    return cuda_fail(e2, "graph instantiate");
+  }
+  memcpy(g->ygraph_key[c], key, sizeof(key));
+  *out = g->ygraph[c];
+  return FDTD_OK;
+}
+
 fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
                     int reset_fields, cudaStream_t s) {
   FDTD_REQUIRE(dt > 0, "dt must be > 0");
@@ -297,12 +358,35 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
   if (p && nsteps) FDTD_CHECK_CUDA(cudaMemsetAsync(y, 0, (size_t)nsteps * p * g->elem, s));
   if (kind == FDTD_KERNEL_PERSIST) return run_yee_stream(g, nsteps, u, y, s);
   const int kchunk = choose_kchunk(g, g->lists.ntx * g->lists.nty, kind == FDTD_KERNEL_TMA ? 3 : 4);
-  for (int64_t n = 0; n < nsteps; ++n) {
+  auto one_step = [&](const void *ur, void *yr) -> fdtd_status {
+    if (kind == FDTD_KERNEL_SPLIT) return launch_yee_split(g, ur, yr, s);
+    if (kind == FDTD_KERNEL_TMA) return launch_yee_tma(g, ur, yr, kchunk, s);
+    return launch_yee(g, ur, yr, kchunk, s);
+  };
+  int64_t n = 0;
+  if (nsteps > 2 * kGraphSteps && !getenv("FDTDMOR_NO_GRAPH")) {
+    // one direct step first (lazily built device tables are made outside any
+    // capture), then whole chunks as replays of a captured graph: u rows are
+    // staged into a fixed buffer before each replay and y rows copied out
+    FDTD_CHECK(one_step(u, y));
+    g->cur ^= 1;
+    n = 1;
+    cudaGraphExec_t exec = nullptr;
+    FDTD_CHECK(step_graph(g, kind, kchunk, s, &exec));
+    const int per_step = kind == FDTD_KERNEL_SPLIT ? 2 : 1;
+    for (; n + kGraphSteps <= nsteps; n += kGraphSteps) {
+      if (m) FDTD_CHECK_CUDA(cudaMemcpyAsync(g->u_graph.ptr, static_cast<const char *>(u) + (size_t)n * m * g->elem,
+                                             (size_t)kGraphSteps * m * g->elem, cudaMemcpyDeviceToDevice, s));
+      FDTD_CHECK_CUDA(cudaGraphLaunch(exec, s));
+      add_launches((int64_t)per_step * kGraphSteps);
+      if (p) FDTD_CHECK_CUDA(cudaMemcpyAsync(static_cast<char *>(y) + (size_t)n * p * g->elem, g->y_graph.ptr,
+                                             (size_t)kGraphSteps * p * g->elem, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  for (; n < nsteps; ++n) {
     const char *ur = u ? static_cast<const char *>(u) + (size_t)n * m * g->elem : nullptr;
     char *yr = y ? static_cast<char *>(y) + (size_t)n * p * g->elem : nullptr;
-    if (kind == FDTD_KERNEL_SPLIT) FDTD_CHECK(launch_yee_split(g, ur, yr, s));
-    else if (kind == FDTD_KERNEL_TMA) FDTD_CHECK(launch_yee_tma(g, ur, yr, kchunk, s));
-    else FDTD_CHECK(launch_yee(g, ur, yr, kchunk, s));
+    FDTD_CHECK(one_step(ur, yr));
     g->cur ^= 1;
   }
   return FDTD_OK;

@@ -329,16 +329,43 @@ __device__ __forceinline__ void h_unit(const YeeArgs<T, ID> &a, int bx, int by, 
   }
 }
 
+// The split kernels are launched as programmatic dependents of the kernel
+// before them: a CTA waits for that grid to complete (and its writes to be
+// visible) before touching memory, and lets the next launch begin once its own
+// work is done, so consecutive launches overlap their launch latency.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename T, typename ID, int VW>
 __global__ void __launch_bounds__(LTX *LTY) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+  wait_prior_grid();
   const int k0 = blockIdx.z * lz;
   e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+  allow_next_grid();
 }
 
 template <typename T, typename ID, bool HOMOG_H, int VW>
 __global__ void __launch_bounds__(LTX *LTY) yee_h_kernel(YeeArgs<T, ID> a, int lz) {
+  wait_prior_grid();
   const int k0 = blockIdx.z * lz;
   h_unit<T, ID, HOMOG_H, false, VW>(a, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+  allow_next_grid();
+}
+
+// Launch with programmatic stream serialisation (see wait_prior_grid).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = getenv("FDTDMOR_NO_PDL") ? 0 : 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Bounded wait until *c >= target (acquire).  Gives up after about a second,
@@ -506,9 +533,10 @@ static fdtd_status launch_split_v(fdtd_grid *g, const void *u_row, void *y_row, 
   const int64_t cols = (int64_t)g->lists.ntx * g->lists.nty * LTX * LTY;
   const int lz = std::min(g->nz, env_int("FDTDMOR_LZ", cols * g->nz >= 4ll * 2048 * device_sms() ? 4 : 1));
   const dim3 grid(g->lists.ntx, g->lists.nty, (g->nz + lz - 1) / lz), block(LTX, LTY);
-  yee_e_kernel<T, ID, VW><<<grid, block, 0, s>>>(a, g->emat.as<ID>(), lz);
+  const ID *emat = g->emat.as<ID>();
+  FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW>, grid, block, s, a, emat, lz));
   FDTD_CHECK(after_launch("yee_e_kernel"));
-  yee_h_kernel<T, ID, HH, VW><<<grid, block, 0, s>>>(a, lz);
+  FDTD_CHECK_CUDA(launch_dependent(yee_h_kernel<T, ID, HH, VW>, grid, block, s, a, lz));
   return after_launch("yee_h_kernel");
 }
 
