@@ -651,11 +651,17 @@ struct BasisBuilder {
   bool last_failed = false;
   int fallbacks = 0;
   std::vector<int> rhs_failed;  // per right-hand side, of the last solve
+  cudaStream_t cap = nullptr;   // private stream the solver iterations are captured on
 
   BasisBuilder(fdtd_grid *g_, const mor_opts &o_, cudaStream_t s_) : g(g_), o(o_), s(s_) {
     nc = g->nc;
     nblk = (int)((nc + MB - 1) / MB);
   }
+  ~BasisBuilder() {
+    if (cap) cudaStreamDestroy(cap);
+  }
+  BasisBuilder(const BasisBuilder &) = delete;
+  BasisBuilder &operator=(const BasisBuilder &) = delete;
 
   // Solve A(z_b) x = (R+F) v for every active right-hand side b (x = [x1; x2]
   // written to out, nb x 6nc).  v: nb x 6nc.
@@ -720,69 +726,103 @@ struct BasisBuilder {
     FDTD_CHECK_CUDA(cudaMemsetAsync(vv, 0, sizeof(cplx<T>) * nb * n3, s));
     solver_scalars_kernel<<<1, 256, 0, s>>>(nb, eblk, part, sc, SM_INIT, o.tol, o.maxit, kMaxRestarts);
     FDTD_CHECK(after_launch("solver_scalars_kernel"));
-    auto scal = [&](int mode, int nbk) -> fdtd_status {
-      solver_scalars_kernel<<<1, 256, 0, s>>>(nb, nbk, part, sc, mode, o.tol, o.maxit, kMaxRestarts);
+    auto scal_on = [&](cudaStream_t st, int mode, int nbk) -> fdtd_status {
+      solver_scalars_kernel<<<1, 256, 0, st>>>(nb, nbk, part, sc, mode, o.tol, o.maxit, kMaxRestarts);
       return after_launch("solver_scalars_kernel");
     };
+    auto scal = [&](int mode, int nbk) { return scal_on(s, mode, nbk); };
     const bool bicg = solver == MOR_SOLVER_BICGSTAB;
     cplx<T> *bh_ = w.bhat.template as<cplx<T>>();
+    // One iteration; converged right-hand sides are frozen by the device-side
+    // scalars, so the iterations need no host decision and are issued in
+    // blocks of `poll` as replays of one captured graph.
+    auto iteration = [&](cudaStream_t st) -> fdtd_status {
+      if (!bicg) {
+        // conjugate gradient squared (right-preconditioned, P = Jacobi)
+        // u = r + beta q; p = u + beta (q + beta p)
+        cgs_update1_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, rr, q, p, u, n3);
+        FDTD_CHECK(after_launch("cgs_update1_kernel"));
+        // v = S P p, sigma = rt^H v
+        h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
+        FDTD_CHECK(after_launch("h_from_e_kernel"));
+        e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, st>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
+        FDTD_CHECK(after_launch("e_from_h_kernel"));
+        FDTD_CHECK(scal_on(st, SM_ALPHA, nblk));
+        // q = u - alpha v; w = u + q (into vv); x += alpha P w
+        cgs_update2_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, u, vv, q, x, P, n3);
+        FDTD_CHECK(after_launch("cgs_update2_kernel"));
+        // r -= alpha S P w; rho = rt^H r; |r|^2
+        h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, vv, n3, P, n3, nullptr, 0, t, n3, nullptr);
+        FDTD_CHECK(after_launch("h_from_e_kernel"));
+        e_from_h_kernel<T, EM_APPLY_RUPDATE><<<grid2, MB, 0, st>>>(ap, t, n3, vv, n3, P, n3, nullptr, 0, rt, rr, n3, sc, part);
+        FDTD_CHECK(after_launch("e_from_h_kernel"));
+        return scal_on(st, SM_CGS_RHO, nblk);
+      }
+      // BiCGSTAB (right-preconditioned, P = Jacobi); p in p, v in vv, s in u, t in q
+      bicg_update_p_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, rr, vv, p, n3);
+      FDTD_CHECK(after_launch("bicg_update_p_kernel"));
+      h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
+      FDTD_CHECK(after_launch("h_from_e_kernel"));
+      e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, st>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
+      FDTD_CHECK(after_launch("e_from_h_kernel"));
+      FDTD_CHECK(scal_on(st, SM_ALPHA, nblk));
+      bicg_update_s_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, rr, vv, u, n3);
+      FDTD_CHECK(after_launch("bicg_update_s_kernel"));
+      h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, u, n3, P, n3, nullptr, 0, t, n3, nullptr);
+      FDTD_CHECK(after_launch("h_from_e_kernel"));
+      // t = S P s with partials s^H t and |t|^2
+      e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, st>>>(ap, t, n3, u, n3, P, n3, q, n3, u, nullptr, n3, sc, part);
+      FDTD_CHECK(after_launch("e_from_h_kernel"));
+      FDTD_CHECK(scal_on(st, SM_OMEGA, nblk));
+      bicg_update_xr_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, P, p, u, q, rt, x, rr, n3, part);
+      FDTD_CHECK(after_launch("bicg_update_xr_kernel"));
+      return scal_on(st, SM_BICG_RHO, eblk);
+    };
     const int poll = 16;
+    cudaGraphExec_t block = nullptr;
+    int64_t block_launches = 0;
+    if (!getenv("FDTDMOR_NO_GRAPH")) {
+      if (!cap) FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      const int64_t before = fdtd_launch_count(0);
+      FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      fdtd_status st = FDTD_OK;
+      for (int k = 0; k < poll && st == FDTD_OK; ++k) st = iteration(cap);
+      block_launches = fdtd_launch_count(0) - before;
+      add_launches(-block_launches);  // captured, not launched
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+      if (st != FDTD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "solver graph capture");
+      const cudaError_t e2 = cudaGraphInstantiate(&block, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "solver graph instantiate");
+    }
+    struct GraphGuard {
+      cudaGraphExec_t &g;
+      ~GraphGuard() { if (g) cudaGraphExecDestroy(g); }
+    } guard{block};
     int it = 0;
     for (int round = 0; round <= kMaxRestarts; ++round) {
-      for (; it < o.maxit + poll; ++it) {
-        if (!bicg) {
-          // conjugate gradient squared (right-preconditioned, P = Jacobi)
-          // u = r + beta q; p = u + beta (q + beta p)
-          cgs_update1_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, q, p, u, n3);
-          FDTD_CHECK(after_launch("cgs_update1_kernel"));
-          // v = S P p, sigma = rt^H v
-          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
-          FDTD_CHECK(after_launch("h_from_e_kernel"));
-          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
-          FDTD_CHECK(after_launch("e_from_h_kernel"));
-          FDTD_CHECK(scal(SM_ALPHA, nblk));
-          // q = u - alpha v; w = u + q (into vv); x += alpha P w
-          cgs_update2_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, u, vv, q, x, P, n3);
-          FDTD_CHECK(after_launch("cgs_update2_kernel"));
-          // r -= alpha S P w; rho = rt^H r; |r|^2
-          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, vv, n3, P, n3, nullptr, 0, t, n3, nullptr);
-          FDTD_CHECK(after_launch("h_from_e_kernel"));
-          e_from_h_kernel<T, EM_APPLY_RUPDATE><<<grid2, MB, 0, s>>>(ap, t, n3, vv, n3, P, n3, nullptr, 0, rt, rr, n3, sc, part);
-          FDTD_CHECK(after_launch("e_from_h_kernel"));
-          FDTD_CHECK(scal(SM_CGS_RHO, nblk));
+      for (; it < o.maxit + poll; it += poll) {
+        if (block) {
+          FDTD_CHECK_CUDA(cudaGraphLaunch(block, s));
+          add_launches(block_launches);
         } else {
-          // BiCGSTAB (right-preconditioned, P = Jacobi); p in p, v in vv, s in u, t in q
-          bicg_update_p_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, vv, p, n3);
-          FDTD_CHECK(after_launch("bicg_update_p_kernel"));
-          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, p, n3, P, n3, nullptr, 0, t, n3, nullptr);
-          FDTD_CHECK(after_launch("h_from_e_kernel"));
-          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, p, n3, P, n3, vv, n3, rt, nullptr, n3, sc, part);
-          FDTD_CHECK(after_launch("e_from_h_kernel"));
-          FDTD_CHECK(scal(SM_ALPHA, nblk));
-          bicg_update_s_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, rr, vv, u, n3);
-          FDTD_CHECK(after_launch("bicg_update_s_kernel"));
-          h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, u, n3, P, n3, nullptr, 0, t, n3, nullptr);
-          FDTD_CHECK(after_launch("h_from_e_kernel"));
-          // t = S P s with partials s^H t and |t|^2
-          e_from_h_kernel<T, EM_APPLY_DOT><<<grid2, MB, 0, s>>>(ap, t, n3, u, n3, P, n3, q, n3, u, nullptr, n3, sc, part);
-          FDTD_CHECK(after_launch("e_from_h_kernel"));
-          FDTD_CHECK(scal(SM_OMEGA, nblk));
-          bicg_update_xr_kernel<T><<<gridE, MB, 0, s>>>(n3, sc, P, p, u, q, rt, x, rr, n3, part);
-          FDTD_CHECK(after_launch("bicg_update_xr_kernel"));
-          FDTD_CHECK(scal(SM_BICG_RHO, eblk));
+          for (int k = 0; k < poll; ++k) FDTD_CHECK(iteration(s));
         }
-        if ((it + 1) % poll == 0) {
-          FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
-          FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
-          bool any = false;
-          for (auto &x2 : hsc) any |= x2.active != 0;
-          if (trace) {
-            fprintf(stderr, "[%s] it %d", bicg ? "bicgstab" : "cgs", it + 1);
-            for (auto &x2 : hsc) fprintf(stderr, " %.3e%s", x2.bn2 > 0 ? std::sqrt(x2.rn2 / x2.bn2) : 0.0, x2.active ? "" : "*");
-            fprintf(stderr, "\n");
-          }
-          if (!any) { ++it; break; }
+        FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+        FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+        bool any = false;
+        for (auto &x2 : hsc) any |= x2.active != 0;
+        if (trace) {
+          fprintf(stderr, "[%s] it %d", bicg ? "bicgstab" : "cgs", it + poll);
+          for (auto &x2 : hsc) fprintf(stderr, " %.3e%s", x2.bn2 > 0 ? std::sqrt(x2.rn2 / x2.bn2) : 0.0, x2.active ? "" : "*");
+          fprintf(stderr, "\n");
         }
+        if (!any) { it += poll; break; }
       }
       // verify with the true residual b - S x; restart the ones above tolerance
       h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, x, n3, nullptr, 0, nullptr, 0, t, n3, nullptr);
