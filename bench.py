@@ -348,6 +348,25 @@ def only_yee(args):
     return 0
 
 
+def only_basis(args):
+    """One Krylov basis build on the 64^3 graded cavity with a small order (the
+    small command used for ncu captures of the shifted-solve kernels)."""
+    import torch
+    from paper_1406_7042_gb300 import fdtdmor as F
+    wl = _workload()
+    grid = F.Grid(wl.grid, "f32")
+    dt0 = wl.s_ref * grid.cfl_dt()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    basis = F.Basis(grid, args.basis_q, dt0, wl.L, wl.M, wl.fmax, tol=args.tol, defl_tol=args.defl_tol,
+                    allow_noconv=True)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"only_basis": wl.name, "q": args.basis_q, "ms": round(a.elapsed_time(b), 3),
+                      "info": basis.info()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,9 +383,13 @@ def main():
     ap.add_argument("--defl-tol", type=float, default=1e-5)
     ap.add_argument("--only-yee", default="", choices=["", "graded", "metascreen", "cavity10"])
     ap.add_argument("--yee-steps", type=int, default=20)
+    ap.add_argument("--only-basis", action="store_true")
+    ap.add_argument("--basis-q", type=int, default=20)
     args = ap.parse_args()
     if args.only_yee:
         return only_yee(args)
+    if args.only_basis:
+        return only_basis(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

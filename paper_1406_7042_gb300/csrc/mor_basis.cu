@@ -348,19 +348,27 @@ __global__ void cgs_update2_kernel(int64_t len, const CgsScal *__restrict__ sc, 
 //   SM_OMEGA:    omega = (t^H s)/(t^H t) from s^H t and |t|^2              (BiCGSTAB)
 //   SM_BICG_RHO: rho' = rt^H r, |r|^2 -> convergence; beta = (rho'/rho)(alpha/omega)
 //   SM_VERIFY:   true residual |b - S x|^2: restart (rt = r) when above tolerance
+// One warp per right-hand side (launch with 32 * nb threads): the warp sums
+// that right-hand side's nblk partial triples in a fixed order (lane-strided,
+// then a shuffle tree), and lane 0 updates its scalars.
 __global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict__ partials, CgsScal *sc,
                                       int mode, double tol, int maxit, int max_restarts) {
-  __shared__ double sh[3 * 32];
-  for (int b = 0; b < nb; ++b) {
-    if (mode != SM_VERIFY && mode != SM_INIT && !sc[b].active) continue;  // uniform across the block
-    if (mode == SM_VERIFY && sc[b].status == 1) continue;                  // iteration cap reached
+  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (b >= nb) return;
+  {
+    if (mode != SM_VERIFY && mode != SM_INIT && !sc[b].active) return;  // uniform across the warp
+    if (mode == SM_VERIFY && sc[b].status == 1) return;                  // iteration cap reached
     double acc[3] = {0, 0, 0};
-    for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
+    for (int blk = lane; blk < nblk; blk += 32) {
       const double *p = partials + ((size_t)b * nblk + blk) * 3;
       acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
     }
-    block_sum(acc, 3, sh);
-    if (threadIdx.x == 0) {
+    for (int o = 16; o; o >>= 1) {
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+      acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+      acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+    }
+    if (lane == 0) {
       CgsScal &s = sc[b];
       const cplx<double> rho(s.rho_re, s.rho_im), d(acc[0], acc[1]);
       auto breakdown = [&]() { s.status = 2; s.active = 0; };
@@ -401,7 +409,6 @@ __global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict
         }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -724,10 +731,10 @@ struct BasisBuilder {
     cgs_init_kernel<T><<<gridE, MB, 0, s>>>(n3, w.bhat.template as<cplx<T>>(), rr, rt, x, p, q, n3, part);
     FDTD_CHECK(after_launch("cgs_init_kernel"));
     FDTD_CHECK_CUDA(cudaMemsetAsync(vv, 0, sizeof(cplx<T>) * nb * n3, s));
-    solver_scalars_kernel<<<1, 256, 0, s>>>(nb, eblk, part, sc, SM_INIT, o.tol, o.maxit, kMaxRestarts);
+    solver_scalars_kernel<<<1, 32 * nb, 0, s>>>(nb, eblk, part, sc, SM_INIT, o.tol, o.maxit, kMaxRestarts);
     FDTD_CHECK(after_launch("solver_scalars_kernel"));
     auto scal_on = [&](cudaStream_t st, int mode, int nbk) -> fdtd_status {
-      solver_scalars_kernel<<<1, 256, 0, st>>>(nb, nbk, part, sc, mode, o.tol, o.maxit, kMaxRestarts);
+      solver_scalars_kernel<<<1, 32 * nb, 0, st>>>(nb, nbk, part, sc, mode, o.tol, o.maxit, kMaxRestarts);
       return after_launch("solver_scalars_kernel");
     };
     auto scal = [&](int mode, int nbk) { return scal_on(s, mode, nbk); };

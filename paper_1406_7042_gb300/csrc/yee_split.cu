@@ -337,7 +337,7 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename T, typename ID, int VW>
-__global__ void __launch_bounds__(LTX *LTY) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+__global__ void __launch_bounds__(LTX *LTY, 3) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
   wait_prior_grid();
   const int k0 = blockIdx.z * lz;
   e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
