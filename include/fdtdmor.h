@@ -105,6 +105,14 @@ FDTD_API fdtd_status fdtd_grid_create(const fdtd_grid_desc *desc, int m, const f
                              fdtd_grid **out);
 FDTD_API fdtd_status fdtd_grid_destroy(fdtd_grid *grid);
 
+/* Replace the material table (same nmat; the per-cell ids are kept), e.g. for
+ * an optimisation loop over eps_r.  Host arrays of nmat values; synchronises
+ * the stream.  The update coefficients and edge properties follow the new
+ * table at the next use. */
+FDTD_API fdtd_status fdtd_grid_set_materials(fdtd_grid *grid, int nmat, const double *eps_r, const double *mu_r,
+                                    const double *sig_e, const double *sig_m, const uint8_t *pec,
+                                    fdtd_stream_t stream);
+
 /* Eq. (CFL): 1/(c sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)) with c = c0/sqrt(min
  * eps_r mu_r) over the non-PEC materials in use and the smallest cell on each
  * axis.  Returns a negative value for a NULL grid. */
@@ -164,6 +172,21 @@ FDTD_API fdtd_status fdtd_fields_set(fdtd_grid *grid, const void *fields6, fdtd_
  * and PEC) and sigma_e (S/m) for Ex, Ey, Ez, then mu (H/m, 0 for H normal to
  * a wall) and sigma_m for Hx, Hy, Hz -- copied to the device buffer dst. */
 FDTD_API fdtd_status fdtd_edge_props_get(fdtd_grid *grid, void *dst, fdtd_stream_t stream);
+
+/* A12 -- gradient of a probe loss L(y) with respect to eps_r by the discrete
+ * adjoint of the leap-frog (Eq. (matrix) differentiated exactly; not in the
+ * paper).  Runs nsteps steps of dt from zero fields with the sources u
+ * (device [nsteps][m], as fdtd_step) keeping ncheckpoints full states
+ * (0: ceil(sqrt(nsteps))), then the adjoint recursion -- the same leap-frog
+ * with the probes as sources driven by dloss_dy (device [nsteps][p], row n =
+ * dL/dy^n) -- back through recomputed segments.  Outputs (device, FP64, either
+ * may be NULL): grad_eps_cell[nc] = dL/d eps_r of each cell (the edge
+ * permittivity being the area-weighted mean of its four cells, Sec. II-A);
+ * grad_eps_mat[nmat] = dL/d eps_r of each material (sum over its cells).
+ * Leaves the grid's fields zeroed.  Extra device memory:
+ * (K + 4) full states + (c + 1) E fields + 3 nc doubles, c = ceil(nsteps / K). */
+FDTD_API fdtd_status fdtd_adjoint(fdtd_grid *grid, double dt, int64_t nsteps, const void *u, const void *dloss_dy,
+                         int ncheckpoints, double *grad_eps_cell, double *grad_eps_mat, fdtd_stream_t stream);
 
 /* Kernel launches issued by the calling thread since the last reset (for
  * launch accounting).  fdtd_launch_count(1) returns the count and resets it. */

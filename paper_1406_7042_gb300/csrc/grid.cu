@@ -153,11 +153,76 @@ static fdtd_status copy_ports(const fdtd_port *in, int n, const fdtd_grid *g,
   return FDTD_OK;
 }
 
+// homog_h (one mu_r, sig_m over the materials in use) and the CFL limit of
+// Eq. (CFL) from the host material table and spacings.
+static void derive_material_props(fdtd_grid *g) {
+  double mu0 = -1, sm0 = -1, emin = 1e300;
+  g->homog_h = true;
+  for (uint16_t i : g->used_mats) {
+    if (mu0 < 0) { mu0 = g->mu_r[i]; sm0 = g->sig_m[i]; }
+    if (g->mu_r[i] != mu0 || g->sig_m[i] != sm0) g->homog_h = false;
+    if (!g->pec[i]) emin = std::min(emin, g->eps_r[i] * g->mu_r[i]);
+  }
+  if (emin > 1e299) emin = 1.0;
+  double dxm = *std::min_element(g->dx.begin(), g->dx.end());
+  double dym = *std::min_element(g->dy.begin(), g->dy.end());
+  double dzm = *std::min_element(g->dz.begin(), g->dz.end());
+  g->cfl = 1.0 / ((kC0 / std::sqrt(emin)) * std::sqrt(1 / (dxm * dxm) + 1 / (dym * dym) + 1 / (dzm * dzm)));
+}
+
+// Raw table (eps_r, sig_e, mu_r, sig_m, pec; 5 x nmat doubles) on the device
+// into mraw and the field-type table mtab.
+static fdtd_status upload_materials(fdtd_grid *g, const double *raw_dev, cudaStream_t s) {
+  const int th = 128;
+  if (g->prec == FDTD_F64)
+    material_table_kernel<double><<<(g->nmat + th - 1) / th, th, 0, s>>>(raw_dev, g->nmat, g->mtab.as<double>());
+  else
+    material_table_kernel<float><<<(g->nmat + th - 1) / th, th, 0, s>>>(raw_dev, g->nmat, g->mtab.as<float>());
+  FDTD_CHECK(after_launch("material_table_kernel"));
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(g->mraw.ptr, raw_dev, (size_t)5 * g->nmat * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return FDTD_OK;
+}
+
 }  // namespace fdtdmor
 
 using namespace fdtdmor;
 
 extern "C" {
+
+fdtd_status fdtd_grid_set_materials(fdtd_grid *g, int nmat, const double *eps_r, const double *mu_r,
+                                    const double *sig_e, const double *sig_m, const uint8_t *pec,
+                                    fdtd_stream_t stream) {
+  FDTD_REQUIRE(g, "fdtd_grid_set_materials: NULL grid");
+  FDTD_REQUIRE(nmat == g->nmat, "fdtd_grid_set_materials: nmat %d differs from the grid's %d", nmat, g->nmat);
+  FDTD_REQUIRE(eps_r && mu_r && sig_e && sig_m && pec, "fdtd_grid_set_materials: missing material table");
+  for (int i = 0; i < nmat; ++i)
+    FDTD_REQUIRE(eps_r[i] > 0 && mu_r[i] > 0 && sig_e[i] >= 0 && sig_m[i] >= 0,
+                 "material %d: need eps_r > 0, mu_r > 0, sigma >= 0", i);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->eps_r.assign(eps_r, eps_r + nmat);
+  g->mu_r.assign(mu_r, mu_r + nmat);
+  g->sig_e.assign(sig_e, sig_e + nmat);
+  g->sig_m.assign(sig_m, sig_m + nmat);
+  g->pec.assign(pec, pec + nmat);
+  derive_material_props(g);
+  std::vector<double> raw;
+  raw.insert(raw.end(), g->eps_r.begin(), g->eps_r.end());
+  raw.insert(raw.end(), g->sig_e.begin(), g->sig_e.end());
+  raw.insert(raw.end(), g->mu_r.begin(), g->mu_r.end());
+  raw.insert(raw.end(), g->sig_m.begin(), g->sig_m.end());
+  for (int i = 0; i < nmat; ++i) raw.push_back(g->pec[i] ? 1.0 : 0.0);
+  DevBuf stage;
+  FDTD_CHECK(stage.alloc(raw.size() * sizeof(double), s));
+  fdtd_status st = FDTD_OK;
+  if (cudaMemcpyAsync(stage.ptr, raw.data(), raw.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "upload materials");
+  if (st == FDTD_OK) st = upload_materials(g, stage.as<double>(), s);
+  if (st == FDTD_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
+  stage.release(s);
+  g->ctab_dt = -1;          // coefficient table and edge properties follow the new table
+  g->eprops_ready = false;
+  return st;
+}
 
 fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *ports, int p,
                              const fdtd_port *probes, fdtd_stream_t stream, fdtd_grid **out) {
@@ -205,20 +270,9 @@ fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *po
     }
     seen[d->mat_id[c]] = 1;
   }
-  double mu0 = -1, sm0 = -1, emin = 1e300;
-  g->homog_h = true;
-  for (int i = 0; i < d->nmat; ++i) {
-    if (!seen[i]) continue;
-    g->used_mats.push_back((uint16_t)i);
-    if (mu0 < 0) { mu0 = g->mu_r[i]; sm0 = g->sig_m[i]; }
-    if (g->mu_r[i] != mu0 || g->sig_m[i] != sm0) g->homog_h = false;
-    if (!g->pec[i]) emin = std::min(emin, g->eps_r[i] * g->mu_r[i]);
-  }
-  if (emin > 1e299) emin = 1.0;
-  double dxm = *std::min_element(g->dx.begin(), g->dx.end());
-  double dym = *std::min_element(g->dy.begin(), g->dy.end());
-  double dzm = *std::min_element(g->dz.begin(), g->dz.end());
-  g->cfl = 1.0 / ((kC0 / std::sqrt(emin)) * std::sqrt(1 / (dxm * dxm) + 1 / (dym * dym) + 1 / (dzm * dzm)));
+  for (int i = 0; i < d->nmat; ++i)
+    if (seen[i]) g->used_mats.push_back((uint16_t)i);
+  derive_material_props(g);
   fdtd_status st;
   if ((st = copy_ports(ports, m, g, g->ports)) != FDTD_OK) return fail(st);
   if ((st = copy_ports(probes, p, g, g->probes)) != FDTD_OK) return fail(st);
@@ -265,17 +319,12 @@ fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *po
   if ((st = g->mraw.alloc((size_t)5 * g->nmat * sizeof(double), s)) != FDTD_OK) return fail(st);
   int th = 128;
   double *raw = dstage.as<double>() + raw_off;
-  if (g->prec == FDTD_F64) {
+  if (g->prec == FDTD_F64)
     axis_tables_kernel<double><<<(ntot + th - 1) / th, th, 0, s>>>(dstage.as<double>(), ntot, g->axis.as<double>(), dstarts.as<int>());
-    if ((st = after_launch("axis_tables_kernel")) != FDTD_OK) return fail(st);
-    material_table_kernel<double><<<(g->nmat + th - 1) / th, th, 0, s>>>(raw, g->nmat, g->mtab.as<double>());
-  } else {
+  else
     axis_tables_kernel<float><<<(ntot + th - 1) / th, th, 0, s>>>(dstage.as<double>(), ntot, g->axis.as<float>(), dstarts.as<int>());
-    if ((st = after_launch("axis_tables_kernel")) != FDTD_OK) return fail(st);
-    material_table_kernel<float><<<(g->nmat + th - 1) / th, th, 0, s>>>(raw, g->nmat, g->mtab.as<float>());
-  }
-  if ((st = after_launch("material_table_kernel")) != FDTD_OK) return fail(st);
-  cudaMemcpyAsync(g->mraw.ptr, raw, (size_t)5 * g->nmat * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if ((st = after_launch("axis_tables_kernel")) != FDTD_OK) return fail(st);
+  if ((st = upload_materials(g, raw, s)) != FDTD_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "grid setup"));
   dstage.release(s);
   dstarts.release(s);

@@ -120,7 +120,8 @@ __global__ void rpf_kernel(OpArgs<T> a, const cplx<T> *__restrict__ v, int64_t v
   if (n >= nc) return;
   const cplx<T> *vb = v + b * vstride;
   cplx<T> *rb = r + b * rstride;
-  const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, a.g.nc, i, j, k);
   auto ld = [&](int64_t idx) { return vb[idx]; };
   for (int c = 0; c < 3; ++c) {
     const int64_t e = c * nc + n;
@@ -144,7 +145,8 @@ __global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int6
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nc = a.g.nc;
   if (n >= nc) return;
-  const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, a.g.nc, i, j, k);
   const cplx<T> *xb = x ? x + b * xstride : nullptr;
   const cplx<T> *pb = P ? P + b * pstride : nullptr;
   auto ld = [&](int64_t idx) { return pb ? pb[idx] * xb[idx] : xb[idx]; };
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
   const int64_t nc = a.g.nc;
   double acc[3] = {0, 0, 0};
   if (n < nc) {
-    const int i = (int)(n % a.g.nx), j = (int)((n / a.g.nx) % a.g.ny), k = (int)(n / ((int64_t)a.g.nx * a.g.ny));
+    int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, a.g.nc, i, j, k);
     const cplx<T> *tb = t + b * tstride;
     auto ld = [&](int64_t idx) { return tb[idx]; };
     const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);

@@ -40,6 +40,21 @@ struct Geo {
   __device__ __forceinline__ int64_t id(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
 };
 
+// (i, j, k) of linear cell index n (x fastest), with 32-bit divisions when the
+// grid has fewer than 2^32 cells.
+__device__ __forceinline__ void cell_ijk(int64_t n, int nx, int ny, int64_t nc, int &i, int &j, int &k) {
+  if (nc <= 0xffffffffll) {
+    const unsigned u = (unsigned)n, q = u / (unsigned)nx;
+    i = (int)(u - q * (unsigned)nx);
+    j = (int)(q % (unsigned)ny);
+    k = (int)(q / (unsigned)ny);
+  } else {
+    i = (int)(n % nx);
+    j = (int)((n / nx) % ny);
+    k = (int)(n / ((int64_t)nx * ny));
+  }
+}
+
 // (curl E)_c at H edge (i, j, k) of a 3-component vector field x (stride nc),
 // values outside the box are zero (tangential E on the PEC walls).
 template <typename T, typename V, typename LD>

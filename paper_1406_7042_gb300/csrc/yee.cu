@@ -282,7 +282,7 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
   if (m) FDTD_CHECK(g->u_graph.alloc((size_t)kGraphSteps * m * g->elem, s));
   if (p) FDTD_CHECK(g->y_graph.alloc((size_t)kGraphSteps * p * g->elem, s));
   double dt = g->ctab_dt;
-  uint64_t key[8] = {(uint64_t)kind, (uint64_t)kchunk ^ ((uint64_t)(uintptr_t)g->ctab.ptr << 8), 0,
+  uint64_t key[8] = {(uint64_t)kind | (uint64_t)g->homog_h << 8, (uint64_t)kchunk ^ ((uint64_t)(uintptr_t)g->ctab.ptr << 8), 0,
                      (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
                      (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr, (uint64_t)(uintptr_t)g->emat.ptr,
                      (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),

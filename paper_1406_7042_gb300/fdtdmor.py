@@ -99,6 +99,11 @@ _SIGS = [
     ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
     ("fdtd_grid_set_kernel", C.c_int, [C.c_void_p, C.c_int]),
+    ("fdtd_grid_set_materials", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint8),
+                                          C.c_void_p]),
+    ("fdtd_adjoint", C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                               C.c_void_p, C.c_void_p]),
     ("mor_opts_default", C.c_int, [C.POINTER(MorOpts)]),
     ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_basis_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -258,6 +263,33 @@ class Grid:
     def set_kernel(self, kernel: str):
         """Leap-frog kernel form: 'auto', 'persist', 'split', 'tma' or 'fused'."""
         check(lib().fdtd_grid_set_kernel(self.h, KERNELS[kernel]))
+
+    def set_materials(self, eps_r, mu_r=None, sig_e=None, sig_m=None, pec=None, stream=None):
+        """Replace the material table (host arrays of nmat values; unspecified
+        columns keep the grid spec's values)."""
+        sp = self.spec
+        cols = []
+        for v, d, dt in ((eps_r, sp.eps_r, np.float64), (mu_r, sp.mu_r, np.float64), (sig_e, sp.sig_e, np.float64),
+                         (sig_m, sp.sig_m, np.float64), (pec, sp.pec, np.uint8)):
+            cols.append(np.ascontiguousarray(np.asarray(d if v is None else v, dtype=dt)))
+        ptr = lambda a, ct: a.ctypes.data_as(C.POINTER(ct))
+        check(lib().fdtd_grid_set_materials(self.h, int(sp.nmat), ptr(cols[0], C.c_double), ptr(cols[1], C.c_double),
+                                            ptr(cols[2], C.c_double), ptr(cols[3], C.c_double),
+                                            ptr(cols[4], C.c_uint8), _stream_ptr(stream)))
+
+    def adjoint(self, dt: float, u, dloss_dy, ncheckpoints: int = 0, per_cell: bool = True,
+                per_material: bool = True, stream=None):
+        """dL/d eps_r by the discrete adjoint: returns (per-cell (nz, ny, nx)
+        FP64 tensor or None, per-material (nmat,) FP64 tensor or None)."""
+        import torch
+        n = int(u.shape[0] if self.m else dloss_dy.shape[0])
+        s = self.spec
+        gc = torch.empty((s.nz, s.ny, s.nx), dtype=torch.float64, device="cuda") if per_cell else None
+        gm = torch.empty((s.nmat,), dtype=torch.float64, device="cuda") if per_material else None
+        check(lib().fdtd_adjoint(self.h, float(dt), n, _dptr(u) if self.m else None,
+                                 _dptr(dloss_dy) if self.p else None, int(ncheckpoints), _dptr(gc), _dptr(gm),
+                                 _stream_ptr(stream)))
+        return gc, gm
 
     def cfl_dt(self) -> float:
         return float(lib().fdtd_cfl_dt(self.h))
@@ -430,3 +462,26 @@ def compare_noalloc(y_red, y_ref, stride: int, offset: int, stream=None) -> floa
     check(lib().mor_compare_noalloc(_dptr(y_red), _dptr(y_ref), int(y_red.shape[0]), int(stride), int(offset),
                                     int(y_red.shape[1]), prec, C.byref(err), _stream_ptr(stream)))
     return err.value
+
+
+def probe_response(grid: "Grid", eps_r, dt: float, u, ncheckpoints: int = 0):
+    """Probe waveforms y (nsteps, p) of `grid` driven by u, as a differentiable
+    function of the per-material relative permittivities eps_r (a torch tensor
+    of nmat values): the forward is fdtd_step after fdtd_grid_set_materials,
+    the backward the discrete adjoint (fdtd_adjoint)."""
+    import torch
+
+    class _ProbeResponse(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, eps):
+            grid.set_materials(eps.detach().cpu().numpy())
+            y = grid.step(dt, u, reset=True)
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            _, gm = grid.adjoint(dt, u, gy.contiguous().to(grid.dtype), ncheckpoints, per_cell=False)
+            return gm.to(eps_r.dtype).to(eps_r.device)
+
+    return _ProbeResponse.apply(eps_r)
+
