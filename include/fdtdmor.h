@@ -140,6 +140,14 @@ typedef enum {
  * FDTD_EINVAL for an unknown value or TMA on a grid it cannot serve. */
 FDTD_API fdtd_status fdtd_grid_set_kernel(fdtd_grid *grid, int kernel);
 
+/* Autotuner of the split form's tile: times trial_steps steps of dt (zero
+ * sources) for every x width (1, 2, 4 cells per thread in FP32; 1, 2 in FP64;
+ * dividing nx) and every z depth (1, 2, 4, 8 planes per thread), keeps the
+ * fastest for later fdtd_step calls on this grid and returns it.  The fields
+ * are restored; the call synchronises the stream. */
+FDTD_API fdtd_status fdtd_grid_autotune(fdtd_grid *grid, double dt, int trial_steps, int *vw_out, int *lz_out,
+                               fdtd_stream_t stream);
+
 /* A2 -- full-order leap-frog, Eq. (matrix) / (MNAform), nsteps steps of dt:
  * E^{n+1} = Ca E^n + Cb (curl H^{n+1/2} - w u^{n+1}),
  * H^{n+3/2} = Da H^{n+1/2} - Db curl E^{n+1}, in the form fdtd_grid_set_kernel
@@ -155,6 +163,18 @@ FDTD_API fdtd_status fdtd_step(fdtd_grid *grid, double dt, int64_t nsteps, const
  * y_host should be pinned for the copies to be asynchronous. */
 FDTD_API fdtd_status fdtd_step_host(fdtd_grid *grid, double dt, int64_t nsteps, const void *u_host,
                            void *y_host, int reset_fields, fdtd_stream_t stream);
+
+/* A11 -- nsteps leap-frog steps of ngrids grids (each with its own dt[q],
+ * sources u[q] (device [nsteps][m_q]) and probes y[q] (device [nsteps][p_q],
+ * zeroed by the call)) advanced together: per step one E and one H launch for
+ * each group of grids sharing field type, id width, uniform mu and x cells per
+ * thread, over a work list of every grid's (tile, z range) units, replayed from
+ * a captured graph in chunks of 16 steps.  Each grid advances exactly as
+ * fdtd_step with its split form would.  reset_fields != 0 zeroes every grid's
+ * state first.  u[q] / y[q] may be NULL for grids without sources / probes;
+ * u / y may be NULL when no grid has any.  A grid may appear once. */
+FDTD_API fdtd_status fdtd_step_batched(fdtd_grid *const *grids, int ngrids, const double *dt, int64_t nsteps,
+                              const void *const *u, void *const *y, int reset_fields, fdtd_stream_t stream);
 
 /* Synchronise the stream and report FDTD_ETIMEOUT if a bounded device-side wait
  * of an earlier fdtd_step on this grid gave up (the flag is then cleared): an

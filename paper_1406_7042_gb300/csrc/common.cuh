@@ -120,11 +120,12 @@ struct fdtd_grid {
   // captured chunks of leap-frog steps (by parity of cur at their start) and
   // what they were captured for; fixed staging rows for their u and y
   cudaGraphExec_t ygraph[2] = {nullptr, nullptr};
-  uint64_t ygraph_key[2][8] = {};
+  uint64_t ygraph_key[2][12] = {};
   cudaStream_t cap_stream = nullptr;
   fdtdmor::DevBuf u_graph, y_graph;
   fdtdmor::DevBuf gsync;        // ticket and per-slab completion counters of the dataflow kernel
   int kernel = 0;               // fdtd_kernel chosen by fdtd_grid_set_kernel (0 = automatic)
+  int tune_vw = 0, tune_lz = 0; // split-kernel tile: x cells per thread, z planes per thread (0 = heuristic)
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
   fdtdmor::DevBuf uflag;        // per (tile, plane) uniform material id or -1 (fast Yee kernel)

@@ -282,12 +282,21 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
   if (m) FDTD_CHECK(g->u_graph.alloc((size_t)kGraphSteps * m * g->elem, s));
   if (p) FDTD_CHECK(g->y_graph.alloc((size_t)kGraphSteps * p * g->elem, s));
   double dt = g->ctab_dt;
-  uint64_t key[8] = {(uint64_t)kind | (uint64_t)g->homog_h << 8, (uint64_t)kchunk ^ ((uint64_t)(uintptr_t)g->ctab.ptr << 8), 0,
-                     (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
-                     (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr, (uint64_t)(uintptr_t)g->emat.ptr,
-                     (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),
-                     (uint64_t)g->lists.tx << 32 | (uint64_t)g->lists.ty};
-  memcpy(&key[2], &dt, sizeof(dt));
+  uint64_t dtbits;
+  memcpy(&dtbits, &dt, sizeof(dt));
+  const bool split = kind == FDTD_KERNEL_SPLIT;
+  uint64_t key[12] = {(uint64_t)kind,
+                      (uint64_t)g->homog_h,
+                      (uint64_t)kchunk,
+                      dtbits,
+                      (uint64_t)(uintptr_t)g->ctab.ptr,
+                      (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
+                      (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr,
+                      (uint64_t)(uintptr_t)g->emat.ptr,
+                      (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),
+                      (uint64_t)g->lists.tx << 32 | (uint64_t)g->lists.ty,
+                      (uint64_t)(split ? yee_split_vw(g) : 0) << 32 | (uint64_t)(split ? yee_split_lz(g) : 0),
+                      (uint64_t)(uintptr_t)g->fields[0].ptr ^ ((uint64_t)(uintptr_t)g->fields[1].ptr << 1)};
   const int c = g->cur;
   if (g->ygraph[c] && memcmp(key, g->ygraph_key[c], sizeof(key)) == 0) {
     *out = g->ygraph[c];
@@ -405,6 +414,62 @@ fdtd_status fdtd_grid_set_kernel(fdtd_grid *g, int kernel) {
   FDTD_REQUIRE(kernel != FDTD_KERNEL_TMA || yee_tma_eligible(g),
                "fdtd_grid_set_kernel: the TMA form needs nx a multiple of %d", g->id_bytes == 1 ? 16 : 8);
   g->kernel = kernel;
+  return FDTD_OK;
+}
+
+fdtd_status fdtd_grid_autotune(fdtd_grid *g, double dt, int trial_steps, int *vw_out, int *lz_out,
+                               fdtd_stream_t stream) {
+  FDTD_REQUIRE(g, "fdtd_grid_autotune: NULL grid");
+  FDTD_REQUIRE(dt > 0 && trial_steps >= 1, "fdtd_grid_autotune: need dt > 0 and trial_steps >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t fbytes = (size_t)6 * g->nc * g->elem;
+  const int m = (int)g->ports.size(), p = (int)g->probes.size();
+  DevBuf save, ub, yb;
+  struct Rel {
+    DevBuf *a, *b, *c;
+    cudaStream_t s;
+    ~Rel() { a->release(s); b->release(s); c->release(s); }
+  } rel{&save, &ub, &yb, s};
+  FDTD_CHECK(save.alloc(fbytes, s));
+  if (m) FDTD_CHECK(ub.alloc((size_t)trial_steps * m * g->elem, s));
+  if (p) FDTD_CHECK(yb.alloc((size_t)trial_steps * p * g->elem, s));
+  if (m) FDTD_CHECK_CUDA(cudaMemsetAsync(ub.ptr, 0, (size_t)trial_steps * m * g->elem, s));
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(save.ptr, g->fields[g->cur].ptr, fbytes, cudaMemcpyDeviceToDevice, s));
+  const int cur0 = g->cur, kind0 = g->kernel;
+  g->kernel = FDTD_KERNEL_SPLIT;
+  cudaEvent_t e0, e1;
+  FDTD_CHECK_CUDA(cudaEventCreate(&e0));
+  FDTD_CHECK_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bvw = 1, blz = 1;
+  fdtd_status st = FDTD_OK;
+  for (int vw = 1; vw <= 16 / g->elem && st == FDTD_OK; vw *= 2) {
+    if (g->nx % vw) continue;
+    for (int lz = 1; lz <= 8 && lz <= std::max(1, g->nz) && st == FDTD_OK; lz *= 2) {
+      g->tune_vw = vw;
+      g->tune_lz = lz;
+      st = yee_run(g, dt, std::min(trial_steps, 4), ub.ptr, yb.ptr, 0, s);  // warm-up, lists, graphs
+      if (st != FDTD_OK) break;
+      cudaEventRecord(e0, s);
+      st = yee_run(g, dt, trial_steps, ub.ptr, yb.ptr, 0, s);
+      cudaEventRecord(e1, s);
+      if (st != FDTD_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bvw = vw; blz = lz; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->kernel = kind0;
+  g->tune_vw = bvw;
+  g->tune_lz = blz;
+  g->cur = cur0;
+  FDTD_CHECK(st);
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fields[g->cur].ptr, save.ptr, fbytes, cudaMemcpyDeviceToDevice, s));
+  if (vw_out) *vw_out = bvw;
+  if (lz_out) *lz_out = blz;
   return FDTD_OK;
 }
 

@@ -99,6 +99,10 @@ _SIGS = [
     ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
     ("fdtd_grid_set_kernel", C.c_int, [C.c_void_p, C.c_int]),
+    ("fdtd_grid_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.c_void_p]),
+    ("fdtd_step_batched", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double), C.c_int64,
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     ("fdtd_grid_set_materials", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint8),
                                           C.c_void_p]),
@@ -291,6 +295,14 @@ class Grid:
                                  _stream_ptr(stream)))
         return gc, gm
 
+    def autotune(self, dt: float, trial_steps: int = 64, stream=None):
+        """Time the split form's tile shapes and keep the fastest; returns
+        (x cells per thread, z planes per thread)."""
+        vw, lz = C.c_int(), C.c_int()
+        check(lib().fdtd_grid_autotune(self.h, float(dt), int(trial_steps), C.byref(vw), C.byref(lz),
+                                       _stream_ptr(stream)))
+        return vw.value, lz.value
+
     def cfl_dt(self) -> float:
         return float(lib().fdtd_cfl_dt(self.h))
 
@@ -462,6 +474,23 @@ def compare_noalloc(y_red, y_ref, stride: int, offset: int, stream=None) -> floa
     check(lib().mor_compare_noalloc(_dptr(y_red), _dptr(y_ref), int(y_red.shape[0]), int(stride), int(offset),
                                     int(y_red.shape[1]), prec, C.byref(err), _stream_ptr(stream)))
     return err.value
+
+
+def step_batched(grids, dts, us, nsteps: int = None, reset: bool = True, stream=None):
+    """Advance several grids together (fdtd_step_batched).  us[q]: (nsteps, m_q)
+    device tensors (or None for a grid without sources); returns the list of
+    probe tensors (nsteps, p_q) (None for a grid without probes)."""
+    import torch
+    n = len(grids)
+    if nsteps is None:
+        nsteps = next(int(u.shape[0]) for u in us if u is not None)
+    ys = [torch.empty((nsteps, g.p), dtype=g.dtype, device="cuda") if g.p else None for g in grids]
+    H = (C.c_void_p * n)(*[g.h.value for g in grids])
+    D = (C.c_double * n)(*[float(d) for d in dts])
+    U = (C.c_void_p * n)(*[_dptr(u) if (u is not None and g.m) else None for g, u in zip(grids, us)])
+    Y = (C.c_void_p * n)(*[_dptr(y) if y is not None else None for y in ys])
+    check(lib().fdtd_step_batched(H, n, D, int(nsteps), U, Y, 1 if reset else 0, _stream_ptr(stream)))
+    return ys
 
 
 def probe_response(grid: "Grid", eps_r, dt: float, u, ncheckpoints: int = 0):
