@@ -219,6 +219,17 @@ FDTD_API int64_t fdtd_launch_count(int reset);
 typedef struct mor_basis mor_basis;
 typedef struct mor_model mor_model;
 
+/* A3 -- the shifted Schur-complement operator of the Krylov solves (Sec. IV-B,
+ * Eqs. (reduced_linear_system_solution1/2)) applied to nb (<= 16) E-field
+ * blocks: y_b = S(z_b) x_b with S(z) x = a11 x + z curlH(curlE(x) / a22),
+ * a11 = (z-1) eps/dt0 + (z+1) sig/2 and a22 = (z-1) mu/dt0 + (z+1) sig_m/2 per
+ * edge -- the rows of A11 - A12 A22^-1 A21 of A(z) = z(R+F) - (R-F) divided
+ * by the edge volumes.  z: host [nb][2] (re, im); x, y: device [nb][3][nc]
+ * complex values of the grid's type (re, im interleaved), Ex, Ey, Ez; dead
+ * edges (walls, PEC) of y are zero.  Allocates one temporary block. */
+FDTD_API fdtd_status mor_schur_apply(fdtd_grid *grid, double dt0, int nb, const double *z, const void *x, void *y,
+                            fdtd_stream_t stream);
+
 /* Arithmetic of the block Gram-Schmidt (CGS2) products of the basis build:
  * the grid's own type, or tensor-core TF32 / BF16 inputs with FP32
  * accumulation (FDTD_F32 grids only).  Gram norms and R factors are FP64. */

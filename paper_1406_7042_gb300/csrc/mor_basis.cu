@@ -1111,6 +1111,38 @@ fdtd_status fdtd_edge_props_get(fdtd_grid *g, void *dst, fdtd_stream_t stream) {
   return FDTD_OK;
 }
 
+fdtd_status mor_schur_apply(fdtd_grid *g, double dt0, int nb, const double *z, const void *x, void *y,
+                            fdtd_stream_t stream) {
+  FDTD_REQUIRE(g && z && x && y, "mor_schur_apply: NULL argument");
+  FDTD_REQUIRE(dt0 > 0, "mor_schur_apply: dt0 must be > 0");
+  FDTD_REQUIRE(nb >= 1 && nb <= kMaxRhs, "mor_schur_apply: nb must be 1..%d", kMaxRhs);
+  cudaStream_t s = (cudaStream_t)stream;
+  FDTD_CHECK(ensure_edge_props(g, s));
+  std::vector<std::complex<double>> zs(nb), one(nb, 1.0);
+  for (int b = 0; b < nb; ++b) zs[b] = std::complex<double>(z[2 * b], z[2 * b + 1]);
+  const int64_t n3 = 3 * g->nc;
+  const int nblk = (int)((g->nc + MB - 1) / MB);
+  const dim3 grid2(nblk, nb);
+  auto run = [&](auto tag) -> fdtd_status {
+    using T = decltype(tag);
+    DevBuf t;
+    FDTD_CHECK(t.alloc((size_t)nb * n3 * sizeof(cplx<T>), s));
+    const OpArgs<T> ah1 = make_op<T>(g, dt0, zs, one), ap = make_op<T>(g, dt0, zs, zs);
+    const cplx<T> *xv = static_cast<const cplx<T> *>(x);
+    h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, xv, n3, nullptr, 0, nullptr, 0, t.as<cplx<T>>(), n3, nullptr);
+    fdtd_status st = after_launch("h_from_e_kernel");
+    if (st == FDTD_OK) {
+      e_from_h_kernel<T, EM_APPLY><<<grid2, MB, 0, s>>>(ap, t.as<cplx<T>>(), n3, xv, n3, nullptr, 0,
+                                                        static_cast<cplx<T> *>(y), n3, nullptr, nullptr, 0, nullptr,
+                                                        nullptr);
+      st = after_launch("e_from_h_kernel");
+    }
+    t.release(s);
+    return st;
+  };
+  return g->prec == FDTD_F64 ? run(double()) : run(float());
+}
+
 fdtd_status mor_basis_destroy(mor_basis *b) {
   if (!b) return FDTD_OK;
   cudaStreamSynchronize(b->stream);

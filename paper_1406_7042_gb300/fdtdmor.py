@@ -109,6 +109,8 @@ _SIGS = [
     ("fdtd_adjoint", C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
     ("mor_opts_default", C.c_int, [C.POINTER(MorOpts)]),
+    ("mor_schur_apply", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
     ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_basis_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_double)]),
@@ -454,6 +456,19 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+def schur_apply(grid: "Grid", dt0: float, z, x, out=None, stream=None):
+    """y_b = S(z_b) x_b (mor_schur_apply): x complex (nb, 3, nz, ny, nx) device
+    tensor of the grid's precision; z: nb complex numbers."""
+    import torch
+    zz = np.asarray(z, np.complex128).ravel()
+    zarr = (C.c_double * (2 * zz.size))(*[v for c in zz for v in (c.real, c.imag)])
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    check(lib().mor_schur_apply(grid.h, float(dt0), int(zz.size), zarr, _dptr(x), _dptr(out), _stream_ptr(stream)))
+    return out
 
 
 def compare(y_red, y_ref, stride: int, offset: int, stream=None) -> float:

@@ -259,3 +259,36 @@ def test_solver_iteration_cap_reports_noconv():
     b = F.Basis(grid, 8, 0.9 * grid.cfl_dt(), 1, 1.1, 50e9, tol=1e-12, maxit=3, allow_noconv=True)
     assert b.status == F.FDTD_ENOCONV
     assert b.info()["max_iters"] == 3
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_schur_apply_matches_oracle(prec, tol):
+    """mor_schur_apply against the oracle's A11 - A12 A22^-1 A21 (rows scaled
+    by the edge volumes), several complex shifts at once."""
+    from oracle import mor
+    g = ragged_grid(nx=20, ny=11, nz=9, seed=41)
+    sys = yee.assemble(g)
+    dt0 = 0.99 * yee.cfl_dt(g)
+    zs = [1.05 * np.exp(0.3j), 0.97 * np.exp(-0.1j), 1.2 + 0j]
+    rng = np.random.default_rng(7)
+    Ne, Nh = sys.Ne, sys.Nh
+    K = sys.K.astype(np.complex128)
+
+    def arrays(v):
+        a = sys.to_arrays(np.concatenate([v, np.zeros(Nh)]))
+        return np.stack([a["Ex"], a["Ey"], a["Ez"]])
+
+    vol = arrays(sys.vol_e)
+    xs, ys = [], []
+    for z in zs:
+        xe = rng.standard_normal(Ne) + 1j * rng.standard_normal(Ne)
+        a11, a22 = mor.schur_blocks(sys, dt0, z)
+        y = a11 * xe - K @ ((-z * (K.T @ xe)) / a22)
+        xs.append(arrays(xe.real) + 1j * arrays(xe.imag))
+        ys.append(arrays(y.real) + 1j * arrays(y.imag))
+    ctype = torch.complex128 if prec == "f64" else torch.complex64
+    grid = F.Grid(g, prec)
+    x = torch.tensor(np.stack(xs), dtype=ctype, device="cuda")
+    yg = F.schur_apply(grid, dt0, zs, x).cpu().numpy() * vol[None]
+    yo = np.stack(ys)
+    assert np.max(np.abs(yg - yo)) <= tol * np.abs(yo).max()
