@@ -119,7 +119,9 @@ struct BatchGroupT : BatchGroup {
       b.p = (int)g->probes.size();
       b.u = static_cast<const T *>(us[q]);
       b.y = static_cast<T *>(ys[q]);
-      const int lz = yee_split_lz(g);
+      // four z planes per thread unless tuned: the batch as a whole has many
+      // waves of units even when each grid alone has few
+      const int lz = g->tune_lz > 0 ? std::min(g->nz, g->tune_lz) : std::min(g->nz, env_int("FDTDMOR_LZ", 4));
       for (int k0 = 0; k0 < g->nz; k0 += lz)
         for (int by = 0; by < g->lists.nty; ++by)
           for (int bx = 0; bx < g->lists.ntx; ++bx) hu.push_back(BatchUnit{(int)q, bx, by, k0, std::min(g->nz, k0 + lz)});
