@@ -235,6 +235,18 @@ FDTD_API fdtd_status mor_schur_apply(fdtd_grid *grid, double dt0, int nb, const 
  * accumulation (FDTD_F32 grids only).  Gram norms and R factors are FP64. */
 typedef enum { MOR_ORTH_NATIVE = 0, MOR_ORTH_TF32 = 1, MOR_ORTH_BF16 = 2 } mor_orth;
 
+/* A6 / A10 -- Gram product G = A^T diag(w) B of tall column-major FP32
+ * matrices, the contraction behind the projection (Eq. (R_and_Freduced)) and
+ * the Gram-Schmidt coefficients: A n x M (column stride lda >= n), B n x N
+ * (ldb >= n), w n weights or NULL, G M x N row-major FP64 (all device).
+ * arith: MOR_ORTH_NATIVE = FP32 CUDA-core products with FP64 sums every 256
+ * rows (needs lda = ldb = n); MOR_ORTH_TF32 / MOR_ORTH_BF16 = tcgen05 tensor
+ * cores with TF32 / BF16 inputs and FP32 accumulation over row chunks, the
+ * chunk sums added in FP64.  M, N <= 65535.  Synchronises the stream;
+ * FDTD_ETIMEOUT if a bounded pipeline wait gave up. */
+FDTD_API fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, const float *B, int64_t ldb,
+                     int N, const float *w, double *G, fdtd_stream_t stream);
+
 /* Krylov solver of the shifted Schur-complement systems.  The paper uses
  * conjugate gradient squared (Sec. IV-B).  AUTO picks it for FDTD_F64 grids
  * and BiCGSTAB for FDTD_F32 grids, where the squared residual polynomial of

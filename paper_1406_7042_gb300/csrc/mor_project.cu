@@ -185,6 +185,9 @@ static fdtd_status gram(cudaStream_t s, int64_t nrows, const T *A, int qa, const
   return after_launch("sum_slices_kernel");
 }
 
+fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
+                        int64_t ldb, int N, const float *w, double *out, unsigned *err);
+
 template <typename T>
 static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, mor_model *M) {
   FDTD_CHECK(ensure_edge_props(g, s));
@@ -254,6 +257,38 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
 using namespace fdtdmor;
 
 extern "C" {
+
+fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, const float *B, int64_t ldb, int N,
+                     const float *w, double *G, fdtd_stream_t stream) {
+  FDTD_REQUIRE(A && B && G, "mor_gram: NULL argument");
+  FDTD_REQUIRE(n >= 1 && M >= 0 && N >= 0 && lda >= n && ldb >= n, "mor_gram: bad sizes");
+  FDTD_REQUIRE(arith == MOR_ORTH_NATIVE || arith == MOR_ORTH_TF32 || arith == MOR_ORTH_BF16,
+               "mor_gram: unknown arithmetic %d", arith);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (arith == MOR_ORTH_NATIVE) {
+    FDTD_REQUIRE(lda == n && ldb == n, "mor_gram: the FP32 path needs lda = ldb = n");
+    DevBuf partial;
+    fdtd_status st = gram<float>(s, n, A, M, B, N, w, partial, G);
+    partial.release(s);
+    return st;
+  }
+  DevBuf flag;
+  FDTD_CHECK(flag.alloc(sizeof(unsigned), s));
+  fdtd_status st = FDTD_OK;
+  if (cudaMemsetAsync(flag.ptr, 0, sizeof(unsigned), s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+  if (st == FDTD_OK)
+    st = gram_tensor(s, arith == MOR_ORTH_BF16, n, A, lda, M, B, ldb, N, w, G, flag.as<unsigned>());
+  unsigned h = 0;
+  if (st == FDTD_OK && cudaMemcpyAsync(&h, flag.ptr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "flag copy");
+  if (st == FDTD_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
+  flag.release(s);
+  if (st == FDTD_OK && h) {
+    set_error("mor_gram: a bounded tensor-core pipeline wait gave up");
+    st = FDTD_ETIMEOUT;
+  }
+  return st;
+}
 
 fdtd_status mor_project(fdtd_grid *g, const mor_basis *b, fdtd_stream_t stream, mor_model **out) {
   FDTD_REQUIRE(g && b && out, "mor_project: NULL argument");

@@ -109,6 +109,8 @@ _SIGS = [
     ("fdtd_adjoint", C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
     ("mor_opts_default", C.c_int, [C.POINTER(MorOpts)]),
+    ("mor_gram", C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                           C.c_void_p, C.c_void_p, C.c_void_p]),
     ("mor_schur_apply", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -456,6 +458,24 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+ORTH = {"native": 0, "tf32": 1, "bf16": 2}
+
+
+def gram(A, B, w=None, arith: str = "tf32", stream=None):
+    """G = A^T diag(w) B (mor_gram) for column-major FP32 device matrices given
+    as (M, n) and (N, n) row-major torch tensors (row r = column r); returns an
+    (M, N) FP64 tensor."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    M, n = A.shape
+    N = B.shape[0]
+    G = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    check(lib().mor_gram(ORTH[arith], int(n), _dptr(A), int(n), int(M), _dptr(B), int(n), int(N),
+                         _dptr(w.contiguous()) if w is not None else None, _dptr(G), _stream_ptr(stream)))
+    return G
 
 
 def schur_apply(grid: "Grid", dt0: float, z, x, out=None, stream=None):
