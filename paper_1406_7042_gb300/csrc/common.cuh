@@ -37,6 +37,14 @@ fdtd_status cuda_fail(cudaError_t e, const char *what);
     }                                        \
   } while (0)
 
+#define FDTD_REQUIRE_STATUS(cond, status, ...) \
+  do {                                         \
+    if (!(cond)) {                             \
+      ::fdtdmor::set_error(__VA_ARGS__);       \
+      return (status);                         \
+    }                                          \
+  } while (0)
+
 // After a kernel launch: count it and surface launch-configuration errors.
 fdtd_status after_launch(const char *name);
 void add_launches(int64_t n);  // kernel launches made by a graph replay

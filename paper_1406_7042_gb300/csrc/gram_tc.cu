@@ -243,13 +243,14 @@ static TcEncodeFn tc_encode() {
   return fn;
 }
 
-// 2-D map over a packed [rows][n_pad] operand, box of 128 bytes x box_rows.
-static fdtd_status tc_map(CUtensorMap *m, bool bf16, void *base, int64_t n_pad, int rows, int box_rows) {
+// 2-D map over a K-major operand of `rows` rows of n values (row stride ld
+// values), box of 128 bytes x box_rows; reads past n or rows are zero.
+static fdtd_status tc_map(CUtensorMap *m, bool bf16, void *base, int64_t n, int64_t ld, int rows, int box_rows) {
   TcEncodeFn fn = tc_encode();
   FDTD_REQUIRE(fn, "cuTensorMapEncodeTiled is not available");
   const int es = bf16 ? 2 : 4;
-  cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)n_pad * es};
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es};
   cuuint32_t box[2] = {(cuuint32_t)(TC_ROWB / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
@@ -262,45 +263,44 @@ static fdtd_status tc_map(CUtensorMap *m, bool bf16, void *base, int64_t n_pad, 
   return FDTD_OK;
 }
 
-// G (M x N, row-major FP64) = A^T diag(w) B on the tensor cores; A: n x M with
-// column stride lda, B: n x N with column stride ldb (FP32, device).
-fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
-                        int64_t ldb, int N, const float *w, double *out, unsigned *err) {
+// dst[c][r] (operand type, row stride n_pad) = (w ? w[r] : 1) src[c * ld + r]
+// for r < n, 0 for n <= r < n_pad; c < ncols.
+fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const float *src, int64_t ld, int ncols,
+                      const float *w, void *dst) {
+  if (ncols == 0) return FDTD_OK;
+  FDTD_REQUIRE(ncols <= 65535, "gram_pack: at most 65535 columns");
+  const int pbk = (int)std::min<int64_t>((n_pad + 255) / 256, 1024);
+  if (bf16)
+    gram_pack_kernel<__nv_bfloat16><<<dim3(pbk, ncols), 256, 0, s>>>(n, n_pad, src, ld, w,
+                                                                     static_cast<__nv_bfloat16 *>(dst));
+  else
+    gram_pack_kernel<float><<<dim3(pbk, ncols), 256, 0, s>>>(n, n_pad, src, ld, w, static_cast<float *>(dst));
+  return after_launch("gram_pack_kernel");
+}
+
+// G (M x N, row-major FP64) = A^T B for K-major operands already in the
+// operand type: A rows (= columns of the original matrix) of n values with
+// row stride lda, B likewise (strides x element size multiples of 16 bytes,
+// 16-byte-aligned bases).  part: scratch for the FP32 partials.
+fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void *A, int64_t lda, int M,
+                               const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part) {
   if (M == 0 || N == 0) return FDTD_OK;
-  FDTD_REQUIRE(M <= 65535 && N <= 65535, "gram_tensor: at most 65535 columns");
-  const int64_t n_pad = std::max<int64_t>(64, (n + 63) / 64 * 64);
   const int es = bf16 ? 2 : 4;
+  FDTD_REQUIRE(M <= 65535 && N <= 65535, "gram_tensor: at most 65535 columns");
+  FDTD_REQUIRE((lda * es) % 16 == 0 && (ldb * es) % 16 == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0,
+               "gram_tensor: operand rows must be 16-byte aligned");
   const int NT = std::min(256, (N + 15) / 16 * 16);
   int tmem_cols = 32;
   while (tmem_cols < NT) tmem_cols *= 2;
   const int mt = (M + TC_M - 1) / TC_M, ntl = (N + NT - 1) / NT;
-  const int kslices = (int)(n_pad * es / TC_ROWB);
+  const int kslices = (int)((n * es + TC_ROWB - 1) / TC_ROWB);
   int nsplit = std::max(1, std::min(kslices, (2 * 152) / std::max(1, mt * ntl)));
   const int per = (kslices + nsplit - 1) / nsplit;
   nsplit = (kslices + per - 1) / per;
-  DevBuf pa, pb, part;
-  struct Rel {
-    DevBuf *a, *b, *c;
-    cudaStream_t s;
-    ~Rel() { a->release(s); b->release(s); c->release(s); }
-  } rel{&pa, &pb, &part, s};
-  FDTD_CHECK(pa.alloc((size_t)M * n_pad * es, s));
-  FDTD_CHECK(pb.alloc((size_t)N * n_pad * es, s));
   FDTD_CHECK(part.alloc((size_t)nsplit * M * N * sizeof(float), s));
-  const int pbk = (int)std::min<int64_t>((n_pad + 255) / 256, 1024);
-  if (bf16) {
-    gram_pack_kernel<__nv_bfloat16><<<dim3(pbk, M), 256, 0, s>>>(n, n_pad, A, lda, nullptr, pa.as<__nv_bfloat16>());
-    FDTD_CHECK(after_launch("gram_pack_kernel"));
-    gram_pack_kernel<__nv_bfloat16><<<dim3(pbk, N), 256, 0, s>>>(n, n_pad, B, ldb, w, pb.as<__nv_bfloat16>());
-  } else {
-    gram_pack_kernel<float><<<dim3(pbk, M), 256, 0, s>>>(n, n_pad, A, lda, nullptr, pa.as<float>());
-    FDTD_CHECK(after_launch("gram_pack_kernel"));
-    gram_pack_kernel<float><<<dim3(pbk, N), 256, 0, s>>>(n, n_pad, B, ldb, w, pb.as<float>());
-  }
-  FDTD_CHECK(after_launch("gram_pack_kernel"));
   CUtensorMap ta, tb;
-  FDTD_CHECK(tc_map(&ta, bf16, pa.ptr, n_pad, M, TC_M));
-  FDTD_CHECK(tc_map(&tb, bf16, pb.ptr, n_pad, N, NT));
+  FDTD_CHECK(tc_map(&ta, bf16, const_cast<void *>(A), n, lda, M, TC_M));
+  FDTD_CHECK(tc_map(&tb, bf16, const_cast<void *>(B), n, ldb, N, NT));
   const size_t smem = 1024 + (size_t)TC_STAGES * (TC_M + NT) * TC_ROWB + 8 * (2 * TC_STAGES + 1) + 16;
   auto kern = bf16 ? gram_tc_kernel<true> : gram_tc_kernel<false>;
   FDTD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -309,6 +309,26 @@ fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, in
   const int MN = M * N;
   gram_tc_sum_kernel<<<(MN + 255) / 256, 256, 0, s>>>(nsplit, MN, part.as<float>(), out);
   return after_launch("gram_tc_sum_kernel");
+}
+
+// G (M x N, row-major FP64) = A^T diag(w) B on the tensor cores; A: n x M with
+// column stride lda, B: n x N with column stride ldb (FP32, device).
+fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
+                        int64_t ldb, int N, const float *w, double *out, unsigned *err) {
+  if (M == 0 || N == 0) return FDTD_OK;
+  const int64_t n_pad = std::max<int64_t>(64, (n + 63) / 64 * 64);
+  const int es = bf16 ? 2 : 4;
+  DevBuf pa, pb, part;
+  struct Rel {
+    DevBuf *a, *b, *c;
+    cudaStream_t s;
+    ~Rel() { a->release(s); b->release(s); c->release(s); }
+  } rel{&pa, &pb, &part, s};
+  FDTD_CHECK(pa.alloc((size_t)M * n_pad * es, s));
+  FDTD_CHECK(pb.alloc((size_t)N * n_pad * es, s));
+  FDTD_CHECK(gram_pack(s, bf16, n, n_pad, A, lda, M, nullptr, pa.ptr));
+  FDTD_CHECK(gram_pack(s, bf16, n, n_pad, B, ldb, N, w, pb.ptr));
+  return gram_tensor_kmajor(s, bf16, n_pad, pa.ptr, n_pad, M, pb.ptr, n_pad, N, out, err, part);
 }
 
 }  // namespace fdtdmor

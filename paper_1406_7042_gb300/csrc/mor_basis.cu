@@ -648,6 +648,33 @@ static OpArgs<T> make_op(fdtd_grid *g, double dt0, const std::vector<std::comple
   return a;
 }
 
+// W[c][r] -= sum_k V[k][r] H[k][c] for r < len, c < nb (H: qc x nb FP64,
+// row-major); V columns of stride ldv, W columns of stride ldw.  H is staged
+// in shared memory as FP32 (kBlkMax columns at most).
+constexpr int kBlkMax = 16;
+template <typename T>
+__global__ void __launch_bounds__(256) block_axpy_kernel(int64_t len, const T *__restrict__ V, int64_t ldv, int qc,
+                                                         const double *__restrict__ H, int nb, T *__restrict__ W,
+                                                         int64_t ldw) {
+  extern __shared__ float hs[];  // [qc][kBlkMax]
+  for (int t = threadIdx.x; t < qc * kBlkMax; t += blockDim.x) {
+    const int k = t / kBlkMax, c = t % kBlkMax;
+    hs[t] = c < nb ? (float)H[(size_t)k * nb + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < len; r += (int64_t)gridDim.x * blockDim.x) {
+    float acc[kBlkMax];
+#pragma unroll
+    for (int c = 0; c < kBlkMax; ++c) acc[c] = 0.0f;
+    for (int k = 0; k < qc; ++k) {
+      const float v = (float)V[(size_t)k * ldv + r];
+#pragma unroll
+      for (int c = 0; c < kBlkMax; ++c) acc[c] += v * hs[k * kBlkMax + c];
+    }
+    for (int c = 0; c < nb; ++c) W[(size_t)c * ldw + r] -= (T)acc[c];
+  }
+}
+
 template <typename T>
 struct BasisBuilder {
   fdtd_grid *g;
@@ -875,11 +902,29 @@ struct BasisBuilder {
     return FDTD_OK;
   }
 
+  // Euclidean norm of vec (FP64 partial sums; synchronises).
+  template <typename V>
+  fdtd_status norm(Work<T> &w, const V *vec, int64_t len, double &out) {
+    const int dblk = (int)((len + 256 * 8 - 1) / (256 * 8));
+    FDTD_CHECK(w.dpart.alloc(sizeof(double) * 2 * (kMaxDots + 1) * dblk, s));
+    double *dp = w.dpart.template as<double>();
+    double *h = w.dots.template as<double>();
+    multidot_kernel<T, V><<<dblk, 256, 0, s>>>(len, vec, 0, 1, vec, dp);
+    FDTD_CHECK(after_launch("multidot_kernel"));
+    reduce_partials_kernel<<<2, 256, 0, s>>>(2, dblk, dp, h);
+    FDTD_CHECK(after_launch("reduce_partials_kernel"));
+    double hh[2];
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(hh, h, sizeof(hh), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    out = std::sqrt(std::max(hh[0], 0.0));
+    return FDTD_OK;
+  }
+
   // Gram-Schmidt of vec (len) against Q[0..nq) (stride qstride), two passes,
   // returns the norm before (n0) and after (n1) via host sync.
   template <typename V>
   fdtd_status cgs2(Work<T> &w, const V *Q, int64_t qstride, int nq, V *vec, int64_t len, double &n0,
-                   double &n1) {
+                   double &n1, int passes = 2) {
     const int dblk = (int)((len + 256 * 8 - 1) / (256 * 8));
     FDTD_CHECK(w.dpart.alloc(sizeof(double) * 2 * (kMaxDots + 1) * dblk, s));
     double *dp = w.dpart.template as<double>();
@@ -896,7 +941,7 @@ struct BasisBuilder {
       return FDTD_OK;
     };
     FDTD_CHECK(norm(n0));
-    for (int pass = 0; pass < 2 && nq > 0; ++pass) {
+    for (int pass = 0; pass < passes && nq > 0; ++pass) {
       for (int c0 = 0; c0 < nq; c0 += kMaxDots) {
         const int cn = std::min(kMaxDots, nq - c0);
         multidot_kernel<T, V><<<dblk, 256, 0, s>>>(len, Q + c0 * qstride, qstride, cn, vec, dp);
@@ -1019,7 +1064,97 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
   DevBuf tmp;
   FDTD_CHECK(tmp.alloc(sizeof(T) * n3, s));
   T *wv = tmp.as<T>();
-  for (int half = 0; half < 2; ++half) {
+  B->orth = sizeof(T) == 4 ? o.orth : MOR_ORTH_NATIVE;
+  if (B->orth != MOR_ORTH_NATIVE) {
+    // Block CGS2 with a tensor-core first pass: pool vectors in blocks of
+    // kBlkMax; the first pass's coefficients H = V^T W come from tcgen05 Gram
+    // products (TF32 or BF16 inputs, FP32 accumulation, FP64 chunk sums)
+    // against a K-major copy of V in the operand type and W -= V H runs on the
+    // CUDA cores; the second pass is the FP32 one; the block's vectors are
+    // then orthonormalised among themselves by CGS2 with the usual deflation
+    // test against their norm before the block projection.
+    const bool bf16 = B->orth == MOR_ORTH_BF16;
+    const int es = bf16 ? 2 : 4;
+    const int64_t n_pad = std::max<int64_t>(64, (n3 + 63) / 64 * 64);
+    DevBuf Vp, Wb, Wp, Hd, part;
+    struct Rel {
+      std::vector<DevBuf *> b;
+      cudaStream_t s;
+      ~Rel() { for (auto *x : b) x->release(s); }
+    } rel{{&Vp, &Wb, &Wp, &Hd, &part}, s};
+    FDTD_CHECK(Vp.alloc((size_t)std::max(1, qmax) * n_pad * es, s));
+    FDTD_CHECK(Wb.alloc((size_t)kBlkMax * n_pad * sizeof(T), s));
+    if (bf16) FDTD_CHECK(Wp.alloc((size_t)kBlkMax * n_pad * es, s));
+    FDTD_CHECK(Hd.alloc((size_t)std::max(1, qmax) * kBlkMax * sizeof(double), s));
+    unsigned *err = g->errflag.as<unsigned>();
+    for (int half = 0; half < 2; ++half) {
+      T *V = (half == 0 ? B->V1 : B->V2).as<T>();
+      std::vector<std::pair<const cplx<T> *, int>> items;
+      for (int pidx = 0; pidx < np; ++pidx) {
+        const int parts = pts[pidx].imag() == 0.0 ? 1 : 2;
+        for (int c = 0; c < ccount[pidx]; ++c)
+          for (int part_ = 0; part_ < parts; ++part_)
+            items.push_back({Qc + ((size_t)pidx * clen + c) * n6 + (half ? n3 : 0), part_});
+      }
+      int qc = 0;
+      for (size_t p0 = 0; p0 < items.size(); p0 += kBlkMax) {
+        const int nbk = (int)std::min<size_t>(kBlkMax, items.size() - p0);
+        T *W = Wb.as<T>();
+        FDTD_CHECK_CUDA(cudaMemsetAsync(W, 0, (size_t)kBlkMax * n_pad * sizeof(T), s));
+        std::vector<double> n0(nbk);
+        for (int c = 0; c < nbk; ++c) {
+          take_part_kernel<T><<<std::min<int64_t>((n3 + 255) / 256, 152 * 16), 256, 0, s>>>(
+              n3, items[p0 + c].first, items[p0 + c].second, W + (size_t)c * n_pad);
+          FDTD_CHECK(after_launch("take_part_kernel"));
+          FDTD_CHECK(bb.norm(w, W + (size_t)c * n_pad, n3, n0[c]));
+        }
+        if (qc > 0) {
+          // first pass: coefficients on the tensor cores
+          const void *Bop = W;
+          if (bf16) {
+            FDTD_CHECK(gram_pack(s, true, n3, n_pad, reinterpret_cast<const float *>(W), n_pad, nbk, nullptr, Wp.ptr));
+            Bop = Wp.ptr;
+          }
+          FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, Vp.ptr, n_pad, qc, Bop, n_pad, nbk, Hd.as<double>(), err, part));
+          const int ablk = (int)std::min<int64_t>((n3 + 255) / 256, 152 * 8);
+          const size_t hsm = sizeof(float) * qc * kBlkMax;
+          FDTD_REQUIRE(hsm <= 227 * 1024, "mor_build_basis: too many basis columns for the block update");
+          if (hsm > 48 * 1024)
+            FDTD_CHECK_CUDA(cudaFuncSetAttribute(block_axpy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)hsm));
+          block_axpy_kernel<T><<<ablk, 256, hsm, s>>>(n3, V, n3, qc, Hd.as<double>(), nbk, W, n_pad);
+          FDTD_CHECK(after_launch("block_axpy_kernel"));
+          // second pass in FP32 with FP64 dot sums restores orthogonality to
+          // the field precision (the cancellation of nearly dependent Krylov
+          // vectors magnifies the first pass's TF32 / BF16 coefficient error)
+          for (int c = 0; c < nbk; ++c) {
+            double a0, a1;
+            FDTD_CHECK(bb.cgs2(w, V, n3, qc, W + (size_t)c * n_pad, n3, a0, a1, 1));
+          }
+        }
+        const int qb0 = qc;
+        for (int c = 0; c < nbk; ++c) {
+          T *wc = W + (size_t)c * n_pad;
+          double m0, n1;
+          FDTD_CHECK(bb.cgs2(w, V + (size_t)qb0 * n3, n3, qc - qb0, wc, n3, m0, n1));
+          if (n0[c] > 0 && n1 >= o.defl_tol * n0[c]) {
+            scale_copy_kernel<T, T><<<std::min<int64_t>((n3 + 255) / 256, 152 * 16), 256, 0, s>>>(
+                n3, wc, V + (size_t)qc * n3, (T)(1.0 / n1));
+            FDTD_CHECK(after_launch("scale_copy_kernel"));
+            FDTD_CHECK(gram_pack(s, bf16, n3, n_pad, reinterpret_cast<const float *>(V + (size_t)qc * n3), n3, 1, nullptr,
+                                 static_cast<char *>(Vp.ptr) + (size_t)qc * n_pad * es));
+            ++qc;
+          }
+        }
+      }
+      (half == 0 ? B->q1 : B->q2) = qc;
+    }
+    unsigned hflag = 0;
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(&hflag, err, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    FDTD_REQUIRE_STATUS(hflag == 0, FDTD_ETIMEOUT, "mor_build_basis: a bounded tensor-core wait gave up");
+  }
+  for (int half = 0; half < 2 && B->orth == MOR_ORTH_NATIVE; ++half) {
     T *V = (half == 0 ? B->V1 : B->V2).as<T>();
     int qc = 0;
     for (int pidx = 0; pidx < np; ++pidx) {

@@ -3,6 +3,14 @@
 #include "mor_common.cuh"
 
 namespace fdtdmor {
+
+// Tensor-core Gram products (gram_tc.cu): G = A^T diag(w) B, FP64 out.
+fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const float *src, int64_t ld, int ncols,
+                      const float *w, void *dst);
+fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void *A, int64_t lda, int M,
+                               const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part);
+fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
+                        int64_t ldb, int N, const float *w, double *out, unsigned *err);
 constexpr int kMaxRhs = 16;   // expansion points x ports solved together
 constexpr int kMaxDots = 64;  // columns per multi-dot pass
 constexpr int kMaxRestarts = 8;  // true-residual restarts of a shifted solve
@@ -27,6 +35,7 @@ struct mor_model : fdtdmor::ModelState {};
 
 struct mor_basis {
   int q1 = 0, q2 = 0;
+  int orth = 0;                 // mor_orth of the Gram-Schmidt products (used again by mor_project)
   int64_t n3 = 0;
   int elem = 4;
   fdtd_prec prec = FDTD_F32;

@@ -185,9 +185,6 @@ static fdtd_status gram(cudaStream_t s, int64_t nrows, const T *A, int qa, const
   return after_launch("sum_slices_kernel");
 }
 
-fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
-                        int64_t ldb, int N, const float *w, double *out, unsigned *err);
-
 template <typename T>
 static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, mor_model *M) {
   FDTD_CHECK(ensure_edge_props(g, s));
@@ -212,16 +209,26 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   FDTD_CHECK(M->BH.alloc(sizeof(double) * std::max(1, q2 * m), s));
   FDTD_CHECK(M->CE.alloc(sizeof(double) * std::max(1, p * q1), s));
   FDTD_CHECK(M->sigma.alloc(sizeof(double) * std::max(1, std::min(q1, q2)), s));
-  FDTD_CHECK(gram<T>(s, n3, V1, q1, V1, q1, w + 0 * n3, partial, M->De.as<double>()));
-  FDTD_CHECK(gram<T>(s, n3, V1, q1, V1, q1, w + 1 * n3, partial, M->Dse.as<double>()));
-  FDTD_CHECK(gram<T>(s, n3, V2, q2, V2, q2, w + 2 * n3, partial, M->Dm.as<double>()));
-  FDTD_CHECK(gram<T>(s, n3, V2, q2, V2, q2, w + 3 * n3, partial, M->Dsm.as<double>()));
+  // the five products on the tensor cores when the basis was built with TF32
+  // or BF16 Gram-Schmidt products (FP32 grids), else FP32 CUDA cores
+  const bool tc = sizeof(T) == 4 && b->orth != MOR_ORTH_NATIVE;
+  auto G = [&](const T *A, int qa, const T *Bm, int qb, const T *wt, double *out) -> fdtd_status {
+    if (tc)
+      return gram_tensor(s, b->orth == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
+                         reinterpret_cast<const float *>(Bm), n3, qb, reinterpret_cast<const float *>(wt), out,
+                         g->errflag.as<unsigned>());
+    return gram<T>(s, n3, A, qa, Bm, qb, wt, partial, out);
+  };
+  FDTD_CHECK(G(V1, q1, V1, q1, w + 0 * n3, M->De.as<double>()));
+  FDTD_CHECK(G(V1, q1, V1, q1, w + 1 * n3, M->Dse.as<double>()));
+  FDTD_CHECK(G(V2, q2, V2, q2, w + 2 * n3, M->Dm.as<double>()));
+  FDTD_CHECK(G(V2, q2, V2, q2, w + 3 * n3, M->Dsm.as<double>()));
   if (q1 && q2) {
     FDTD_CHECK(W.alloc(sizeof(T) * (size_t)q2 * n3, s));
     dim3 grid(bl, q2);
     kv_kernel<T><<<grid, 256, 0, s>>>(make_geo<T>(g), g->eprops.as<T>(), V2, W.as<T>());
     FDTD_CHECK(after_launch("kv_kernel"));
-    FDTD_CHECK(gram<T>(s, n3, V1, q1, W.as<T>(), q2, nullptr, partial, M->K.as<double>()));
+    FDTD_CHECK(G(V1, q1, W.as<T>(), q2, nullptr, M->K.as<double>()));
   }
   // B~_E (q1 x m) from the source edges, C~_E (p x q1) from the probe edges
   std::vector<PortEdge> src, prb;
@@ -244,6 +251,12 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   if (q1 && p) {
     port_gather_kernel<T><<<q1, 256, sizeof(double) * p, s>>>(make_geo<T>(g), V1, n3, q1, dprb.as<PortEdge>(), (int64_t)prb.size(), p, 1, M->CE.as<double>());
     FDTD_CHECK(after_launch("port_gather_kernel"));
+  }
+  if (tc) {
+    unsigned hflag = 0;
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(&hflag, g->errflag.ptr, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    FDTD_REQUIRE_STATUS(hflag == 0, FDTD_ETIMEOUT, "mor_project: a bounded tensor-core wait gave up");
   }
   // the unperturbed K~ is also the working K~' until mor_perturb runs
   FDTD_CHECK_CUDA(cudaMemcpyAsync(M->Kp.ptr, M->K.ptr, sizeof(double) * q1 * q2, cudaMemcpyDeviceToDevice, s));

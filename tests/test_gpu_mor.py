@@ -292,3 +292,31 @@ def test_schur_apply_matches_oracle(prec, tol):
     yg = F.schur_apply(grid, dt0, zs, x).cpu().numpy() * vol[None]
     yo = np.stack(ys)
     assert np.max(np.abs(yg - yo)) <= tol * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("orth,ortho_tol,span_tol", [("tf32", 2e-5, 2e-3), ("bf16", 2e-5, 2e-2)])
+def test_tensor_core_gram_schmidt_basis(orth, ortho_tol, span_tol):
+    """Basis with the first CGS2 pass on the tcgen05 tensor cores (TF32 / BF16
+    inputs) and the second in FP32: orthonormality at FP32 level, the spanned
+    space matches the FP32 basis, and the projected model (tensor-core Gram
+    products too) matches the FP32 one."""
+    g = ragged_grid(nx=24, ny=13, nz=11, seed=61)
+    grid = F.Grid(g, "f32")
+    dt0 = 0.99 * grid.cfl_dt()
+    kw = dict(L=1, M=1.1, fmax=40e9, tol=1e-6, defl_tol=1e-5)
+    bn = F.Basis(grid, 24, dt0, orth="native", **kw)
+    bt = F.Basis(grid, 24, dt0, orth=orth, **kw)
+    for which in (1, 2):
+        Vn = bn.V(which).double()
+        Vt = bt.V(which).double()
+        assert Vt.shape == Vn.shape
+        eye = torch.eye(Vt.shape[0], dtype=torch.float64, device="cuda")
+        assert float((Vt @ Vt.T - eye).abs().max()) <= ortho_tol
+        resid = Vn - (Vn @ Vt.T) @ Vt          # native columns outside span(Vt)
+        assert float(resid.norm() / Vn.norm()) <= span_tol
+    mn, mt = F.Model(grid, bn), F.Model(grid, bt)
+    for name in ("De", "Dm", "K"):
+        a, b = mn.get(name), mt.get(name)
+        # same subspaces, possibly different bases: compare invariants
+        sa, sb = np.linalg.svd(a, compute_uv=False), np.linalg.svd(b, compute_uv=False)
+        assert np.max(np.abs(sa - sb)) <= 10 * span_tol * sa.max(), name
