@@ -277,6 +277,9 @@ def run_ours(args):
         line["yee_hbm"] = hbm_grid_measure(F, W, hbm)
     if rank == 0 and args.batch:
         line["batch"] = batch_measure(F, W)
+    if rank == 0 and args.tensor:
+        line["tensor_gram"] = tensor_gram_measure(F, peaks)
+        line["precision_study"] = precision_study(F, W)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl, dt0, args.cpu_seconds)
     if rank == 0:
@@ -351,6 +354,75 @@ def batch_measure(F, W, nsteps=200):
             "batched_Mcell_updates_per_s": round(cells * nsteps / ms_b / 1e3, 1),
             "separate_calls_Mcell_updates_per_s": round(cells * nsteps / ms_s / 1e3, 1),
             "batched_ms": round(ms_b, 3), "separate_ms": round(ms_s, 3)}
+
+
+def tensor_gram_measure(F, peaks, n=786432, q=200, reps=5):
+    """mor_gram G = V^T V on the tcgen05 tensor cores (TF32 and BF16 inputs)
+    and on the FP32 CUDA cores, for a basis-shaped n x q FP32 matrix (n = 3 x
+    64^3 edges, q = 200 columns), timed with CUDA events.  FLOPs 2 n q^2;
+    algorithmic bytes: V read once for A and once for B (8 n q)."""
+    import torch
+    V = torch.randn((q, n), dtype=torch.float32, device="cuda")
+    out = {}
+    bf16_peak = peaks.get("bf16_tflops", 1864.6)
+    for arith in ("native", "tf32", "bf16"):
+        F.gram(V, V, None, arith)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            F.gram(V, V, None, arith)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        tf = 2.0 * n * q * q / (ms / 1e3) / 1e12
+        peak = bf16_peak if arith == "bf16" else (bf16_peak * 1.1 / 2.25 if arith == "tf32" else None)
+        out[arith] = {"ms": round(ms, 4), "TFLOP_s": round(tf, 2), "GB_s": round(8.0 * n * q / (ms / 1e3) / 1e9, 1),
+                      "tensor_peak_TFLOP_s": round(peak, 1) if peak else None,
+                      "note": "TF32 reads V in place; BF16 includes packing V once; synchronous call"}
+    out["shape"] = {"n": n, "q": q}
+    out["peak_source"] = ("of measured: MEASURED_PEAKS.json bf16_tflops (burst), TF32 = bf16 x 1.1/2.25 nominal ratio"
+                          if "bf16_tflops" in peaks else "of fallback 1.9 PFLOP/s bf16")
+    return out
+
+
+def precision_study(F, W):
+    """The 100x50x24 microstrip (q = 100): basis and projection with FP32,
+    TF32 and BF16 Gram-Schmidt products; reduced-model probe error at
+    s = 0.99 against the FP64 full-order run of the same grid."""
+    import torch
+    wl = W.config4(downscale=True)
+    g = wl.grid
+    ref = F.Grid(g, "f64")
+    dt0 = wl.s_ref * ref.cfl_dt()
+    n = wl.nsteps_ref
+    u64 = torch.tensor(W.excitation(g, wl.f0, wl.bw, dt0, n), dtype=torch.float64, device="cuda")
+    yref = ref.step(dt0, u64, reset=True)
+    grid = F.Grid(g, "f32")
+    u32 = u64.float()
+    out = {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "q": wl.q, "steps": n}
+    yfd = grid.step(dt0, u32, reset=True)
+    out["fdtd_f32_err"] = round(F.compare(yfd, yref.float(), 1, 0), 8)
+    y_native = None
+    for orth in ("native", "tf32", "bf16"):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        basis = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=1e-5, defl_tol=1e-5, orth=orth, allow_noconv=True)
+        model = F.Model(grid, basis)
+        b.record()
+        torch.cuda.synchronize()
+        model.perturb(dt0)
+        yr = model.run(u32)
+        V1 = basis.V(1).double()
+        ortho = float((V1 @ V1.T - torch.eye(V1.shape[0], dtype=torch.float64, device="cuda")).abs().max())
+        if y_native is None:
+            y_native = yr.clone()
+        out[orth] = {"err_vs_fp64_fdtd": round(F.compare(yr, yref.float(), 1, 0), 6),
+                     "diff_vs_fp32_basis_model": round(F.compare(yr, y_native, 1, 0), 6),
+                     "basis_plus_projection_ms": round(a.elapsed_time(b), 1), "q1": basis.info()["q1"],
+                     "orthonormality_max_abs": ortho}
+        del model, basis
+    return out
 
 
 def accuracy_sweep(F, W, wl, grid, model, yref, dt0, nref):
@@ -450,6 +522,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hbm-grid", type=int, default=1)
     ap.add_argument("--batch", type=int, default=1, help="measure the batched cavity workload")
+    ap.add_argument("--tensor", type=int, default=1, help="tensor-core Gram throughput and the precision study")
     ap.add_argument("--mor", type=int, default=1, help="include the reduction stages in the bench step")
     ap.add_argument("--tol", type=float, default=1e-4, help="shifted-solve residual limit (Sec. IV-B: 1e-4)")
     ap.add_argument("--defl-tol", type=float, default=1e-5)
@@ -457,12 +530,18 @@ def main():
     ap.add_argument("--yee-steps", type=int, default=20)
     ap.add_argument("--only-basis", action="store_true")
     ap.add_argument("--only-batch", action="store_true")
+    ap.add_argument("--only-tensor", action="store_true")
     ap.add_argument("--basis-q", type=int, default=20)
     args = ap.parse_args()
     if args.only_yee:
         return only_yee(args)
     if args.only_basis:
         return only_basis(args)
+    if args.only_tensor:
+        from paper_1406_7042_gb300 import fdtdmor as F
+        from paper_1406_7042_gb300 import workloads as W
+        print(json.dumps({"tensor_gram": tensor_gram_measure(F, _peaks()), "precision_study": precision_study(F, W)}))
+        return 0
     if args.only_batch:
         from paper_1406_7042_gb300 import fdtdmor as F
         from paper_1406_7042_gb300 import workloads as W

@@ -324,11 +324,28 @@ fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, in
     cudaStream_t s;
     ~Rel() { a->release(s); b->release(s); c->release(s); }
   } rel{&pa, &pb, &part, s};
-  FDTD_CHECK(pa.alloc((size_t)M * n_pad * es, s));
-  FDTD_CHECK(pb.alloc((size_t)N * n_pad * es, s));
-  FDTD_CHECK(gram_pack(s, bf16, n, n_pad, A, lda, M, nullptr, pa.ptr));
-  FDTD_CHECK(gram_pack(s, bf16, n, n_pad, B, ldb, N, w, pb.ptr));
-  return gram_tensor_kmajor(s, bf16, n_pad, pa.ptr, n_pad, M, pb.ptr, n_pad, N, out, err, part);
+  // FP32 operands whose rows are already 16-byte aligned are read in place
+  // (the tensor map zero-fills past n); others are packed once each
+  auto aligned = [](const float *p, int64_t ld) { return (ld * 4) % 16 == 0 && ((uintptr_t)p % 16) == 0; };
+  const void *pA = A, *pB = B;
+  int64_t la = lda, lb = ldb, nk = n;
+  const bool a_direct = !bf16 && aligned(A, lda), b_direct = !bf16 && !w && aligned(B, ldb);
+  if (!(a_direct && b_direct)) {
+    nk = n_pad;
+    FDTD_CHECK(pa.alloc((size_t)M * n_pad * es, s));
+    FDTD_CHECK(gram_pack(s, bf16, n, n_pad, A, lda, M, nullptr, pa.ptr));
+    pA = pa.ptr;
+    la = n_pad;
+    if (B == A && ldb == lda && N == M && !w) {
+      pB = pa.ptr;
+    } else {
+      FDTD_CHECK(pb.alloc((size_t)N * n_pad * es, s));
+      FDTD_CHECK(gram_pack(s, bf16, n, n_pad, B, ldb, N, w, pb.ptr));
+      pB = pb.ptr;
+    }
+    lb = n_pad;
+  }
+  return gram_tensor_kmajor(s, bf16, nk, pA, la, M, pB, lb, N, out, err, part);
 }
 
 }  // namespace fdtdmor
