@@ -8,10 +8,11 @@
 // folded into B, rows padded with zeros to a multiple of 64), which gives the
 // tensor memory accelerator 16-byte-aligned rows.  Each CTA owns a 128 x NT
 // tile of G and a contiguous range of 128-byte K slices: one thread streams
-// the A and B boxes (128-byte swizzle) through a 4-stage shared-memory ring
-// with cp.async.bulk.tensor and issues tcgen05.mma into a TMEM accumulator
-// (128 lanes x NT columns of FP32); tcgen05.commit releases each stage when
-// the MMAs reading it complete.  The epilogue reads the accumulator with
+// the A and B boxes (128-byte swizzle) through a shared-memory ring of up to 8
+// stages
+// with cp.async.bulk.tensor, another issues tcgen05.mma into a TMEM
+// accumulator (128 lanes x NT columns of FP32); tcgen05.commit releases each
+// stage to the loader when the MMAs reading it complete.  The epilogue reads the accumulator with
 // tcgen05.ld and writes the CTA's FP32 partial; a second kernel adds the
 // partials of all K ranges in FP64 in a fixed order.  Every mbarrier wait is
 // bounded: on a timeout the CTA sets the error flag, waits (bounded) for its
@@ -26,7 +27,7 @@
 namespace fdtdmor {
 
 constexpr int TC_M = 128;        // rows of a G tile (TMEM lanes)
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 8;
 constexpr int TC_ROWB = 128;     // bytes of K per row of a box (one swizzle row)
 constexpr int TC_THREADS = 128;
 
@@ -104,7 +105,8 @@ template <bool BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap ta,
                                                               const __grid_constant__ CUtensorMap tb, int M, int N,
                                                               int NT, int tmem_cols, int kslices, int per,
-                                                              float *__restrict__ partial, unsigned *err) {
+                                                              int TC_STAGES, float *__restrict__ partial,
+                                                              unsigned *err) {
   extern __shared__ unsigned char tc_raw[];
   const uint32_t base = (tc_smem(tc_raw) + 1023u) & ~1023u;
   const uint32_t a_bytes = TC_M * TC_ROWB, b_bytes = (uint32_t)NT * TC_ROWB;
@@ -140,39 +142,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(slot_ptr);
 
+  // warp 0 lane 0 streams the boxes, warp 1 lane 0 issues the MMAs
   bool ok = true;
   if (threadIdx.x == 0 && nk > 0) {
-    // producer and MMA issuer in one thread, TC_STAGES loads in flight
-    auto load = [&](int it) {
+    for (int it = 0; it < nk; ++it) {
       const int s = it % TC_STAGES;
+      if (it >= TC_STAGES && !tc_wait(empty + 8 * s, (uint32_t)((it / TC_STAGES) + 1) & 1u)) {
+        ok = false;
+        break;
+      }
       const uint32_t sa = base + s * stage_bytes, sb = sa + a_bytes;
       tc_expect_tx(full + 8 * s, stage_bytes);
       const int kx = (ks0 + it) * KEL;
       tc_tma_2d(sa, &ta, kx, m0, full + 8 * s);
       tc_tma_2d(sb, &tb, kx, n0, full + 8 * s);
-    };
-    for (int it = 0; it < min(nk, TC_STAGES); ++it) load(it);
-    for (int it = 0; it < nk && ok; ++it) {
+    }
+    if (!ok) atomicOr(err, 4u);
+  } else if (threadIdx.x == 32 && nk > 0) {
+    for (int it = 0; it < nk; ++it) {
       const int s = it % TC_STAGES;
-      const uint32_t par = (uint32_t)(it / TC_STAGES) & 1u;
-      if (!tc_wait(full + 8 * s, par)) { ok = false; break; }
+      if (!tc_wait(full + 8 * s, (uint32_t)(it / TC_STAGES) & 1u)) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = base + s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
       for (int kk = 0; kk < TC_ROWB / 32; ++kk)   // 32 bytes of K per MMA (8 TF32 / 16 BF16)
         tc_mma<BF16>(tmem, tc_desc(sa + 32 * kk), tc_desc(sb + 32 * kk), idesc, (it > 0 || kk > 0) ? 1u : 0u);
       tc_commit(empty + 8 * s);
-      if (it + TC_STAGES < nk) {
-        if (!tc_wait(empty + 8 * s, par)) { ok = false; break; }
-        load(it + TC_STAGES);
-      }
     }
-    tc_commit(done);
+    tc_commit(done);   // also after a timeout: completes once the issued MMAs have
     if (!ok) atomicOr(err, 4u);
   }
   // epilogue: every thread owns one row of the tile
   const bool have = nk > 0 && tc_wait(done, 0);
   if (!have && nk > 0 && threadIdx.x == 0) atomicOr(err, 4u);
+  ok = have;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int m = m0 + warp * 32 + lane;
   float *prow = partial + ((size_t)blockIdx.z * M + m) * N;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const __grid_con
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int n = n0 + c + q;
-        if (n < N && c + q < NT) prow[n] = (have && ok) ? __uint_as_float(r[q]) : 0.0f;
+        if (n < N && c + q < NT) prow[n] = ok ? __uint_as_float(r[q]) : 0.0f;
       }
     }
   }
@@ -294,17 +300,24 @@ fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void 
   while (tmem_cols < NT) tmem_cols *= 2;
   const int mt = (M + TC_M - 1) / TC_M, ntl = (N + NT - 1) / NT;
   const int kslices = (int)((n * es + TC_ROWB - 1) / TC_ROWB);
-  int nsplit = std::max(1, std::min(kslices, (2 * 152) / std::max(1, mt * ntl)));
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int nsplit = std::max(1, std::min(kslices, std::max(1, sms) / std::max(1, mt * ntl)));  // one wave
   const int per = (kslices + nsplit - 1) / nsplit;
   nsplit = (kslices + per - 1) / per;
   FDTD_CHECK(part.alloc((size_t)nsplit * M * N * sizeof(float), s));
   CUtensorMap ta, tb;
   FDTD_CHECK(tc_map(&ta, bf16, const_cast<void *>(A), n, lda, M, TC_M));
   FDTD_CHECK(tc_map(&tb, bf16, const_cast<void *>(B), n, ldb, N, NT));
-  const size_t smem = 1024 + (size_t)TC_STAGES * (TC_M + NT) * TC_ROWB + 8 * (2 * TC_STAGES + 1) + 16;
+  // as many stages as fit in 220 KB of shared memory
+  const size_t stage = (size_t)(TC_M + NT) * TC_ROWB;
+  const int nst = (int)std::max<size_t>(2, std::min<size_t>(TC_MAX_STAGES, (220 * 1024 - 1024 - 256) / stage));
+  const size_t smem = 1024 + (size_t)nst * stage + 8 * (2 * nst + 1) + 16;
   auto kern = bf16 ? gram_tc_kernel<true> : gram_tc_kernel<false>;
   FDTD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<dim3(mt, ntl, nsplit), TC_THREADS, smem, s>>>(ta, tb, M, N, NT, tmem_cols, kslices, per, part.as<float>(), err);
+  kern<<<dim3(mt, ntl, nsplit), TC_THREADS, smem, s>>>(ta, tb, M, N, NT, tmem_cols, kslices, per, nst, part.as<float>(),
+                                                       err);
   FDTD_CHECK(after_launch("gram_tc_kernel"));
   const int MN = M * N;
   gram_tc_sum_kernel<<<(MN + 255) / 256, 256, 0, s>>>(nsplit, MN, part.as<float>(), out);

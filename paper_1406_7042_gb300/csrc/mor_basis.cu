@@ -1086,7 +1086,11 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
     FDTD_CHECK(Wb.alloc((size_t)kBlkMax * n_pad * sizeof(T), s));
     if (bf16) FDTD_CHECK(Wp.alloc((size_t)kBlkMax * n_pad * es, s));
     FDTD_CHECK(Hd.alloc((size_t)std::max(1, qmax) * kBlkMax * sizeof(double), s));
-    unsigned *err = g->errflag.as<unsigned>();
+    DevBuf tflag;  // set by a tensor-core pipeline wait that gave up
+    rel.b.push_back(&tflag);
+    FDTD_CHECK(tflag.alloc(sizeof(unsigned), s));
+    FDTD_CHECK_CUDA(cudaMemsetAsync(tflag.ptr, 0, sizeof(unsigned), s));
+    unsigned *err = tflag.as<unsigned>();
     for (int half = 0; half < 2; ++half) {
       T *V = (half == 0 ? B->V1 : B->V2).as<T>();
       std::vector<std::pair<const cplx<T> *, int>> items;

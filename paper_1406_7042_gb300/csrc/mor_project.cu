@@ -212,11 +212,16 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   // the five products on the tensor cores when the basis was built with TF32
   // or BF16 Gram-Schmidt products (FP32 grids), else FP32 CUDA cores
   const bool tc = sizeof(T) == 4 && b->orth != MOR_ORTH_NATIVE;
+  DevBuf tflag;  // set by a tensor-core pipeline wait that gave up
+  if (tc) {
+    FDTD_CHECK(tflag.alloc(sizeof(unsigned), s));
+    FDTD_CHECK_CUDA(cudaMemsetAsync(tflag.ptr, 0, sizeof(unsigned), s));
+  }
   auto G = [&](const T *A, int qa, const T *Bm, int qb, const T *wt, double *out) -> fdtd_status {
     if (tc)
       return gram_tensor(s, b->orth == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
                          reinterpret_cast<const float *>(Bm), n3, qb, reinterpret_cast<const float *>(wt), out,
-                         g->errflag.as<unsigned>());
+                         tflag.as<unsigned>());
     return gram<T>(s, n3, A, qa, Bm, qb, wt, partial, out);
   };
   FDTD_CHECK(G(V1, q1, V1, q1, w + 0 * n3, M->De.as<double>()));
@@ -254,8 +259,9 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   }
   if (tc) {
     unsigned hflag = 0;
-    FDTD_CHECK_CUDA(cudaMemcpyAsync(&hflag, g->errflag.ptr, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(&hflag, tflag.ptr, sizeof(hflag), cudaMemcpyDeviceToHost, s));
     FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    tflag.release(s);
     FDTD_REQUIRE_STATUS(hflag == 0, FDTD_ETIMEOUT, "mor_project: a bounded tensor-core wait gave up");
   }
   // the unperturbed K~ is also the working K~' until mor_perturb runs
