@@ -316,8 +316,11 @@ def schur_roofline(F, wl, grid, dt0, hbm, peak_src, reps=50):
     ms = a.elapsed_time(b) / reps
     byts = g.ncells * (120.0 * nb + 48.0)
     ach = byts / (ms / 1e3) / 1e9
+    # DRAM bytes per launch of the pair from one ncu capture of `bench.py
+    # --only-schur` (dram__bytes_read.sum + dram__bytes_write.sum of both kernels)
+    traffic = 25152768 + 0 + 43403008 + 44800
     return {"kernel": "h_from_e_kernel + e_from_h_kernel (Schur-complement apply, mor_schur_apply)", "bound": "hbm",
-            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
             "peak_source": peak_src, "rhs": nb, "ms_per_launch": round(ms, 4),
             "bytes_per_launch": int(byts),
             "note": "dominant kernel pair of the step (basis build); 64^3 blocks of complex RHS, one per expansion point"}
@@ -531,12 +534,31 @@ def main():
     ap.add_argument("--only-basis", action="store_true")
     ap.add_argument("--only-batch", action="store_true")
     ap.add_argument("--only-tensor", action="store_true")
+    ap.add_argument("--only-gram", action="store_true")
+    ap.add_argument("--only-schur", action="store_true")
     ap.add_argument("--basis-q", type=int, default=20)
     args = ap.parse_args()
     if args.only_yee:
         return only_yee(args)
     if args.only_basis:
         return only_basis(args)
+    if args.only_gram:
+        import torch
+        from paper_1406_7042_gb300 import fdtdmor as F
+        V = torch.randn((200, 786432), dtype=torch.float32, device="cuda")
+        for arith in ("tf32", "bf16"):
+            F.gram(V, V, None, arith)
+        torch.cuda.synchronize()
+        print(json.dumps({"only_gram": "tf32 and bf16 V^T V, n = 786432, q = 200"}))
+        return 0
+    if args.only_schur:
+        import torch
+        from paper_1406_7042_gb300 import fdtdmor as F
+        wl = _workload()
+        grid = F.Grid(wl.grid, "f32")
+        dt0 = wl.s_ref * grid.cfl_dt()
+        print(json.dumps({"only_schur": schur_roofline(F, wl, grid, dt0, _peaks().get("hbm_gbs", 6800.0), "", reps=20)}))
+        return 0
     if args.only_tensor:
         from paper_1406_7042_gb300 import fdtdmor as F
         from paper_1406_7042_gb300 import workloads as W
