@@ -318,7 +318,7 @@ def schur_roofline(F, wl, grid, dt0, hbm, peak_src, reps=50):
     ach = byts / (ms / 1e3) / 1e9
     # DRAM bytes per launch of the pair from one ncu capture of `bench.py
     # --only-schur` (dram__bytes_read.sum + dram__bytes_write.sum of both kernels)
-    traffic = 25152768 + 0 + 43403008 + 44800
+    traffic = 25164032 + 0 + 43603712 + 11520
     return {"kernel": "h_from_e_kernel + e_from_h_kernel (Schur-complement apply, mor_schur_apply)", "bound": "hbm",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
             "peak_source": peak_src, "rhs": nb, "ms_per_launch": round(ms, 4),

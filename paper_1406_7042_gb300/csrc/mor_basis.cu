@@ -151,6 +151,8 @@ __global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int6
   const cplx<T> *pb = P ? P + b * pstride : nullptr;
   auto ld = [&](int64_t idx) { return pb ? pb[idx] * xb[idx] : xb[idx]; };
   const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+  cplx<T> ce[3];
+  if (xb) curl_e3<T, cplx<T>>(a.g, ld, i, j, k, n, ce);
   for (int c = 0; c < 3; ++c) {
     const int64_t e = c * nc + n;
     const T mu = a.mu[e];
@@ -158,7 +160,7 @@ __global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int6
     if (mu != T(0)) {
       cplx<T> num;
       if (r2) num = r2[b * r2stride + e];
-      if (xb) num = num + a.cz[b] * curl_e_at<T, cplx<T>>(a.g, ld, c, i, j, k);
+      if (xb) num = num + a.cz[b] * ce[c];
       const cplx<T> a22 = (mu * a.inv_dt) * zm1 + (T(0.5) * a.sgm[e]) * zp1;
       out = cdiv(num, a22);
     }
@@ -213,12 +215,16 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
   double acc[3] = {0, 0, 0};
   if (n < nc) {
     int i, j, k;
-  cell_ijk(n, a.g.nx, a.g.ny, a.g.nc, i, j, k);
+    cell_ijk(n, a.g.nx, a.g.ny, a.g.nc, i, j, k);
     const cplx<T> *tb = t + b * tstride;
     auto ld = [&](int64_t idx) { return tb[idx]; };
     const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
     cplx<T> alpha;
     if (MODE == EM_APPLY_RUPDATE) alpha = cplx<T>((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+    cplx<T> ch[3];
+    curl_h3<T, cplx<T>>(a.g, ld, i, j, k, n, ch);
+    // this cell's three terms of each dot product, summed in the field type
+    T s0 = 0, s1 = 0, s2 = 0;
     for (int c = 0; c < 3; ++c) {
       const int64_t e = c * nc + n;
       const T ep = a.eps[e];
@@ -232,32 +238,35 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
           const cplx<T> px = P ? P[b * pstride + e] * x[b * xstride + e] : x[b * xstride + e];
           A = a11 * px;
         }
-        out = A + a.cz[b] * curl_h_at<T, cplx<T>>(a.g, ld, c, i, j, k);
+        out = A + a.cz[b] * ch[c];
       }
       if (MODE == EM_APPLY_DOT) {
         const cplx<T> w = conj(rt[b * rstride + e]) * out;
-        acc[0] += (double)w.re;
-        acc[1] += (double)w.im;
-        acc[2] += (double)norm2(out);
+        s0 += w.re;
+        s1 += w.im;
+        s2 += norm2(out);
         y[b * ystride + e] = out;
       } else if (MODE == EM_RESID) {
         cplx<T> rv = rt[b * rstride + e] - out;
         if (ep == T(0)) rv = cplx<T>();
         y[b * ystride + e] = rv;
-        acc[0] += (double)norm2(rv);
-        acc[2] += (double)norm2(rv);
+        s0 += norm2(rv);
+        s2 += norm2(rv);
       } else if (MODE == EM_APPLY_RUPDATE) {
         cplx<T> rv = r[b * rstride + e] - alpha * out;
         if (ep == T(0)) rv = cplx<T>();
         r[b * rstride + e] = rv;
         const cplx<T> w = conj(rt[b * rstride + e]) * rv;
-        acc[0] += (double)w.re;
-        acc[1] += (double)w.im;
-        acc[2] += (double)norm2(rv);
+        s0 += w.re;
+        s1 += w.im;
+        s2 += norm2(rv);
       } else {
         y[b * ystride + e] = out;
       }
     }
+    acc[0] = (double)s0;
+    acc[1] = (double)s1;
+    acc[2] = (double)s2;
   }
   if (MODE == EM_APPLY_DOT || MODE == EM_APPLY_RUPDATE || MODE == EM_RESID) {
     block_sum(acc, 3, sh);
@@ -362,7 +371,8 @@ __global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict
     if (mode != SM_VERIFY && mode != SM_INIT && !sc[b].active) return;  // uniform across the warp
     if (mode == SM_VERIFY && sc[b].status == 1) return;                  // iteration cap reached
     double acc[3] = {0, 0, 0};
-    for (int blk = lane; blk < nblk; blk += 32) {
+#pragma unroll 8
+    for (int blk = lane; blk < nblk; blk += 32) {  // unrolled: the loads go out together
       const double *p = partials + ((size_t)b * nblk + blk) * 3;
       acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
     }
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__(MB) bicg_update_xr_kernel(int64_t len, const C
   const int b = blockIdx.y;
   if (!sc[b].active) return;
   const cplx<T> al((T)sc[b].alpha_re, (T)sc[b].alpha_im), om((T)sc[b].omega_re, (T)sc[b].omega_im);
-  double acc[3] = {0, 0, 0};
+  T s0 = 0, s1 = 0, s2 = 0;  // this thread's few terms in the field type, then FP64
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = b * stride + e;
     const cplx<T> pw = P[o];
@@ -476,8 +486,9 @@ __global__ void __launch_bounds__(MB) bicg_update_xr_kernel(int64_t len, const C
     const cplx<T> rv = sv[o] - om * tv[o];
     r[o] = rv;
     const cplx<T> w = conj(rt[o]) * rv;
-    acc[0] += (double)w.re; acc[1] += (double)w.im; acc[2] += (double)norm2(rv);
+    s0 += w.re; s1 += w.im; s2 += norm2(rv);
   }
+  double acc[3] = {(double)s0, (double)s1, (double)s2};
   block_sum(acc, 3, sh);
   if (threadIdx.x == 0) {
     double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
@@ -988,7 +999,9 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
   FDTD_CHECK(w.v.alloc(cb * nb * n6, s));
   FDTD_CHECK(w.r.alloc(cb * nb * n6, s));
   for (DevBuf *d : {&w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t}) FDTD_CHECK(d->alloc(cb * nb * n3, s));
-  FDTD_CHECK(w.partials.alloc(sizeof(double) * 3 * nb * (size_t)bb.nblk, s));
+  // one partial triple per CTA of the widest reducing kernel (operator: one
+  // CTA per MB cells; vector updates: up to 16 CTAs per SM)
+  FDTD_CHECK(w.partials.alloc(sizeof(double) * 3 * nb * (size_t)std::max(bb.nblk, 152 * 16), s));
   FDTD_CHECK(w.sc.alloc(sizeof(CgsScal) * nb, s));
   FDTD_CHECK(w.dots.alloc(sizeof(double) * 2 * (kMaxDots + 1), s));
   // chains: per point, k*m complex vectors of 6nc

@@ -96,6 +96,38 @@ __device__ __forceinline__ V curl_h_at(const Geo<T> &g, LD ld, int c, int i, int
   }
 }
 
+// All three components of curl E at cell (i, j, k) (linear index n) from the
+// nine values they need, each loaded once (values outside the box are zero).
+template <typename T, typename V, typename LD>
+__device__ __forceinline__ void curl_e3(const Geo<T> &g, LD ld, int i, int j, int k, int64_t n, V out[3]) {
+  const int64_t nc = g.nc, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  const V z(0);
+  const bool ip = i + 1 < g.nx, jp = j + 1 < g.ny, kp = k + 1 < g.nz;
+  const V ex = ld(n), ey = ld(nc + n), ez = ld(2 * nc + n);
+  const V ez_jp = jp ? ld(2 * nc + n + sy) : z, ey_kp = kp ? ld(nc + n + sz) : z;
+  const V ex_kp = kp ? ld(n + sz) : z, ez_ip = ip ? ld(2 * nc + n + 1) : z;
+  const V ey_ip = ip ? ld(nc + n + 1) : z, ex_jp = jp ? ld(n + sy) : z;
+  const T rx = g.rd(0, i), ry = g.rd(1, j), rz = g.rd(2, k);
+  out[0] = ry * (ez_jp - ez) - rz * (ey_kp - ey);
+  out[1] = rz * (ex_kp - ex) - rx * (ez_ip - ez);
+  out[2] = rx * (ey_ip - ey) - ry * (ex_jp - ex);
+}
+
+// All three components of curl H at cell (i, j, k), each input loaded once.
+template <typename T, typename V, typename LD>
+__device__ __forceinline__ void curl_h3(const Geo<T> &g, LD ld, int i, int j, int k, int64_t n, V out[3]) {
+  const int64_t nc = g.nc, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  const V z(0);
+  const V hx = ld(n), hy = ld(nc + n), hz = ld(2 * nc + n);
+  const V hz_jm = j > 0 ? ld(2 * nc + n - sy) : z, hy_km = k > 0 ? ld(nc + n - sz) : z;
+  const V hx_km = k > 0 ? ld(n - sz) : z, hz_im = i > 0 ? ld(2 * nc + n - 1) : z;
+  const V hy_im = i > 0 ? ld(nc + n - 1) : z, hx_jm = j > 0 ? ld(n - sy) : z;
+  const T rx = g.rdd(0, i), ry = g.rdd(1, j), rz = g.rdd(2, k);
+  out[0] = ry * (hz - hz_jm) - rz * (hy - hy_km);
+  out[1] = rz * (hx - hx_km) - rx * (hz - hz_im);
+  out[2] = rx * (hy - hy_im) - ry * (hx - hx_jm);
+}
+
 // Per-edge material properties of a grid (computed once, field type T) in
 // g->eprops: E edges: eps (absolute, 0 on dead edges: walls / PEC), sig;
 // H edges: mu (absolute, 0 on dead edges: normal to a wall), sgm; each 3 x nc.
