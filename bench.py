@@ -481,6 +481,7 @@ def only_yee(args):
     grid = F.Grid(wl.grid, prec)
     dt = wl.s_ref * grid.cfl_dt()
     n = args.yee_steps
+    tuned = grid.autotune(dt, 200) if args.autotune else None
     u = torch.tensor(W.excitation(wl.grid, wl.f0, wl.bw, dt, n), dtype=grid.dtype, device="cuda")
     y = grid.step(dt, u, reset=True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -490,7 +491,7 @@ def only_yee(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / max(1, n)
     print(json.dumps({"only_yee": wl.name, "steps": n, "ms_per_launch": round(ms, 5),
-                      "Mcell_updates_per_s": round(wl.grid.ncells / ms / 1e3, 1)}))
+                      "Mcell_updates_per_s": round(wl.grid.ncells / ms / 1e3, 1), "tuned_vw_lz": tuned}))
     return 0
 
 
@@ -535,6 +536,7 @@ def main():
     ap.add_argument("--only-batch", action="store_true")
     ap.add_argument("--only-tensor", action="store_true")
     ap.add_argument("--only-gram", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="with --only-yee: tune the tile first")
     ap.add_argument("--only-schur", action="store_true")
     ap.add_argument("--basis-q", type=int, default=20)
     args = ap.parse_args()

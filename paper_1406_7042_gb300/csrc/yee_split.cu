@@ -26,7 +26,7 @@
 namespace fdtdmor {
 
 template <typename T, typename ID, int VW>
-__global__ void __launch_bounds__(LTX *LTY, 3) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+__global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 3 : 4) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
   wait_prior_grid();
   const int k0 = blockIdx.z * lz;
   e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
@@ -79,7 +79,7 @@ __device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, u
 // flight together, E^{n+1} and H^{n+1/2} of a slab are still in L2 when its H
 // units run, so DRAM sees each field read once and written once per step.
 template <typename T, typename ID, bool HOMOG_H, int VW>
-__global__ void __launch_bounds__(LTX *LTY, 2) yee_stream_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
+__global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 2 : 4) yee_stream_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
                                                               int nslab, int64_t nsteps, const T *u, int m, T *y,
                                                               int p, unsigned *cnt, unsigned *err) {
   __shared__ long long s_ticket;
@@ -134,16 +134,16 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_stream_kernel(YeeArgs<T, ID> 
   }
 }
 
-// Cells per thread along x: the widest of 16, 8 bytes whose vectors divide
-// the rows (every vector load is then aligned) and whose 32-lane tile is not
-// wider than a row, else 1.
+// Cells per thread along x: 2 when they divide the rows (every vector load is
+// then aligned) and the 32-lane tile is not wider than a row, else 1.
 // A tuned width (fdtd_grid_autotune) takes precedence.
 int yee_split_vw(const fdtd_grid *g) {
   if (g->tune_vw > 0) return g->tune_vw;
   if (getenv("FDTDMOR_NO_VEC")) return 1;
-  for (int v = 16 / (int)g->elem; v >= 2; v /= 2)
-    if (g->nx % v == 0 && 32 * v <= g->nx) return v;
-  return 1;
+  // 2 cells per thread: measured faster than 4 (FP32) at the occupancy the
+  // register budget allows (fdtd_grid_autotune can pick 4)
+  const int v = 2;
+  return g->nx % v == 0 && 32 * v <= g->nx ? v : 1;
 }
 
 // z planes per thread of the split launches: tuned, else 4 once the grid has
