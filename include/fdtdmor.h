@@ -127,13 +127,18 @@ FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
  * allows.  TMA: one
  * fused launch per step staging planes through shared memory with the tensor
  * memory accelerator (needs nx a multiple of 16 for uint8 ids, 8 for uint16).
- * FUSED: one fused launch per step with plain loads into shared memory. */
+ * FUSED: one fused launch per step with plain loads into shared memory.
+ * MARCH: one fused launch per step without block barriers: each thread
+ * marches z, updating H one plane behind E and recomputing the two
+ * neighbouring E values its H update needs; sources and probes follow in two
+ * small launches (the step is linear). */
 typedef enum {
   FDTD_KERNEL_AUTO = 0,
   FDTD_KERNEL_PERSIST = 1,
   FDTD_KERNEL_SPLIT = 2,
   FDTD_KERNEL_TMA = 3,
-  FDTD_KERNEL_FUSED = 4
+  FDTD_KERNEL_FUSED = 4,
+  FDTD_KERNEL_MARCH = 5
 } fdtd_kernel;
 
 /* Choose the kernel form for later fdtd_step calls on this grid.

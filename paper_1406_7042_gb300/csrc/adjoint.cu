@@ -137,12 +137,24 @@ struct AdjointView {
   int *cur;
   TileLists *lists;
   std::vector<HostPort> *ports, *probes;
+  DevBuf fsrc, fprb;             // the adjoint run's flat port lists (fused z-march form)
+  int nfsrc = 0, nfprb = 0;
+  bool fready = false;
   AdjointView(fdtd_grid *g_, DevBuf *f, int *c, TileLists *l, std::vector<HostPort> *pt, std::vector<HostPort> *pb)
       : g(g_), fields(f), cur(c), lists(l), ports(pt), probes(pb) {
     swap_all();
   }
-  ~AdjointView() { swap_all(); }
+  ~AdjointView() {
+    swap_all();
+    fsrc.release(g->create_stream);
+    fprb.release(g->create_stream);
+  }
   void swap_all() {
+    std::swap(g->flat_src, fsrc);
+    std::swap(g->flat_prb, fprb);
+    std::swap(g->nflat_src, nfsrc);
+    std::swap(g->nflat_prb, nfprb);
+    std::swap(g->flat_ready, fready);
     std::swap(g->fields[0], fields[0]);
     std::swap(g->fields[1], fields[1]);
     std::swap(g->cur, *cur);

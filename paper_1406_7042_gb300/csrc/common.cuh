@@ -129,11 +129,15 @@ struct fdtd_grid {
   // what they were captured for; fixed staging rows for their u and y
   cudaGraphExec_t ygraph[2] = {nullptr, nullptr};
   uint64_t ygraph_key[2][12] = {};
+  int64_t ygraph_launches[2] = {0, 0};
   cudaStream_t cap_stream = nullptr;
   fdtdmor::DevBuf u_graph, y_graph;
   fdtdmor::DevBuf gsync;        // ticket and per-slab completion counters of the dataflow kernel
   int kernel = 0;               // fdtd_kernel chosen by fdtd_grid_set_kernel (0 = automatic)
   int tune_vw = 0, tune_lz = 0; // split-kernel tile: x cells per thread, z planes per thread (0 = heuristic)
+  fdtdmor::DevBuf flat_src, flat_prb;  // flat (cell, comp, port, w) lists of the fused z-march form
+  int nflat_src = 0, nflat_prb = 0;
+  bool flat_ready = false;
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
   fdtdmor::DevBuf uflag;        // per (tile, plane) uniform material id or -1 (fast Yee kernel)

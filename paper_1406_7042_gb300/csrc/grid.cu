@@ -354,6 +354,8 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->emat.release(s);
   g->gsync.release(s);
   g->u_graph.release(s);
+  g->flat_src.release(s);
+  g->flat_prb.release(s);
   g->y_graph.release(s);
   for (auto &x : g->ygraph)
     if (x) cudaGraphExecDestroy(x);

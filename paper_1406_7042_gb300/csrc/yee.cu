@@ -277,14 +277,15 @@ constexpr int kGraphSteps = 32;
 
 // The graph of kGraphSteps steps starting from parity g->cur, captured on a
 // private stream the first time and whenever what it baked in has changed.
-static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s, cudaGraphExec_t *out) {
+static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s, cudaGraphExec_t *out,
+                              int64_t *launches) {
   const int m = (int)g->ports.size(), p = (int)g->probes.size();
   if (m) FDTD_CHECK(g->u_graph.alloc((size_t)kGraphSteps * m * g->elem, s));
   if (p) FDTD_CHECK(g->y_graph.alloc((size_t)kGraphSteps * p * g->elem, s));
   double dt = g->ctab_dt;
   uint64_t dtbits;
   memcpy(&dtbits, &dt, sizeof(dt));
-  const bool split = kind == FDTD_KERNEL_SPLIT;
+  const bool split = kind == FDTD_KERNEL_SPLIT || kind == FDTD_KERNEL_MARCH;
   uint64_t key[12] = {(uint64_t)kind,
                       (uint64_t)g->homog_h,
                       (uint64_t)kchunk,
@@ -300,6 +301,7 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
   const int c = g->cur;
   if (g->ygraph[c] && memcmp(key, g->ygraph_key[c], sizeof(key)) == 0) {
     *out = g->ygraph[c];
+    *launches = g->ygraph_launches[c];
     return FDTD_OK;
   }
   if (g->ygraph[c]) {
@@ -317,12 +319,14 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
     const char *ur = m ? static_cast<const char *>(g->u_graph.ptr) + (size_t)n * m * g->elem : nullptr;
     char *yr = p ? static_cast<char *>(g->y_graph.ptr) + (size_t)n * p * g->elem : nullptr;
     if (kind == FDTD_KERNEL_SPLIT) st = launch_yee_split(g, ur, yr, cs);
+    else if (kind == FDTD_KERNEL_MARCH) st = launch_yee_march(g, ur, yr, cs);
     else if (kind == FDTD_KERNEL_TMA) st = launch_yee_tma(g, ur, yr, kchunk, cs);
     else st = launch_yee(g, ur, yr, kchunk, cs);
     g->cur ^= 1;
   }
   g->cur = c;
-  add_launches(launches_before - fdtd_launch_count(0));  // captured, not launched
+  const int64_t captured = fdtd_launch_count(0) - launches_before;
+  add_launches(-captured);  // captured, not launched
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (st != FDTD_OK) {
@@ -337,7 +341,9 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
     return cuda_fail(e2, "graph instantiate");
   }
   memcpy(g->ygraph_key[c], key, sizeof(key));
+  g->ygraph_launches[c] = captured;
   *out = g->ygraph[c];
+  *launches = captured;
   return FDTD_OK;
 }
 
@@ -352,13 +358,14 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
   if (const char *e = getenv("FDTDMOR_YEE")) {  // override for measurements
     const std::string v(e);
     kind = v == "persist" ? FDTD_KERNEL_PERSIST : v == "split" ? FDTD_KERNEL_SPLIT
-         : v == "tma" ? FDTD_KERNEL_TMA : v == "fused" ? FDTD_KERNEL_FUSED : kind;
+         : v == "tma" ? FDTD_KERNEL_TMA : v == "fused" ? FDTD_KERNEL_FUSED
+         : v == "march" ? FDTD_KERNEL_MARCH : kind;
   }
   if (kind == FDTD_KERNEL_TMA && !yee_tma_eligible(g)) kind = FDTD_KERNEL_FUSED;
   if (kind == FDTD_KERNEL_AUTO) kind = FDTD_KERNEL_SPLIT;
   int ttx = YTX, tty = YTY;
   if (kind == FDTD_KERNEL_TMA) yee_tma_tile(&ttx, &tty);
-  if (kind == FDTD_KERNEL_PERSIST || kind == FDTD_KERNEL_SPLIT) ttx = 32 * yee_split_vw(g);
+  if (kind == FDTD_KERNEL_PERSIST || kind == FDTD_KERNEL_SPLIT || kind == FDTD_KERNEL_MARCH) ttx = 32 * yee_split_vw(g);
   FDTD_CHECK(build_tile_lists(g, ttx, tty, s));
   if (reset_fields) {
     FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)6 * g->nc * g->elem, s));
@@ -369,6 +376,7 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
   const int kchunk = choose_kchunk(g, g->lists.ntx * g->lists.nty, kind == FDTD_KERNEL_TMA ? 3 : 4);
   auto one_step = [&](const void *ur, void *yr) -> fdtd_status {
     if (kind == FDTD_KERNEL_SPLIT) return launch_yee_split(g, ur, yr, s);
+    if (kind == FDTD_KERNEL_MARCH) return launch_yee_march(g, ur, yr, s);
     if (kind == FDTD_KERNEL_TMA) return launch_yee_tma(g, ur, yr, kchunk, s);
     return launch_yee(g, ur, yr, kchunk, s);
   };
@@ -381,13 +389,13 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
     g->cur ^= 1;
     n = 1;
     cudaGraphExec_t exec = nullptr;
-    FDTD_CHECK(step_graph(g, kind, kchunk, s, &exec));
-    const int per_step = kind == FDTD_KERNEL_SPLIT ? 2 : 1;
+    int64_t per_replay = 0;
+    FDTD_CHECK(step_graph(g, kind, kchunk, s, &exec, &per_replay));
     for (; n + kGraphSteps <= nsteps; n += kGraphSteps) {
       if (m) FDTD_CHECK_CUDA(cudaMemcpyAsync(g->u_graph.ptr, static_cast<const char *>(u) + (size_t)n * m * g->elem,
                                              (size_t)kGraphSteps * m * g->elem, cudaMemcpyDeviceToDevice, s));
       FDTD_CHECK_CUDA(cudaGraphLaunch(exec, s));
-      add_launches((int64_t)per_step * kGraphSteps);
+      add_launches(per_replay);
       if (p) FDTD_CHECK_CUDA(cudaMemcpyAsync(static_cast<char *>(y) + (size_t)n * p * g->elem, g->y_graph.ptr,
                                              (size_t)kGraphSteps * p * g->elem, cudaMemcpyDeviceToDevice, s));
     }
@@ -409,7 +417,7 @@ extern "C" {
 
 fdtd_status fdtd_grid_set_kernel(fdtd_grid *g, int kernel) {
   FDTD_REQUIRE(g, "fdtd_grid_set_kernel: NULL grid");
-  FDTD_REQUIRE(kernel >= FDTD_KERNEL_AUTO && kernel <= FDTD_KERNEL_FUSED, "fdtd_grid_set_kernel: unknown kernel %d",
+  FDTD_REQUIRE(kernel >= FDTD_KERNEL_AUTO && kernel <= FDTD_KERNEL_MARCH, "fdtd_grid_set_kernel: unknown kernel %d",
                kernel);
   FDTD_REQUIRE(kernel != FDTD_KERNEL_TMA || yee_tma_eligible(g),
                "fdtd_grid_set_kernel: the TMA form needs nx a multiple of %d", g->id_bytes == 1 ? 16 : 8);

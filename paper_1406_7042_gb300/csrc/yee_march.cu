@@ -1,0 +1,379 @@
+// A2 (large grids): the Yee leap-frog of Eq. (matrix) fused into one pass over
+// memory per step, with no block barriers and no shared memory.
+//
+// Each thread owns VW consecutive x cells of one row of a 32 VW x 8 tile and
+// marches up a chunk of z planes.  At plane k it computes E^{n+1}(k) for its
+// cells and, from the same input buffer, the two E^{n+1} components its H
+// update needs from outside: Ex, Ez of the row above (j + 1, recomputed by
+// this thread) and Ey, Ez of the next x cell (the next lane's own value by a
+// shuffle; the last lane recomputes it).  It then updates H^{n+3/2} one plane
+// behind, at k - 1, from E^{n+1} at k - 1 and k, so every value a thread needs
+// is its own or its neighbour's in the warp.  A chunk's top plane is computed
+// once more by the chunk above; nothing else is recomputed.  The new state
+// goes to the other buffer (ping-pong), so neighbours always read the old one.
+//
+// DRAM sees each field value read once and written once per step (the 48 B
+// per cell of the fused form, plus the material map); the recomputed halo
+// reads come from L1/L2.  Sources and probes are applied afterwards by two
+// small kernels: the step is linear, so a source's effect on this step's H is
+// -Db curlE(dE) on the four H edges around the source edge.
+#include <algorithm>
+#include <vector>
+
+#include "yee_units.cuh"
+
+namespace fdtdmor {
+
+// One E^{n+1} component (without sources) at any cell, zero outside the box:
+// Ca E^n + Cb (curl H^{n+1/2})_c, coefficients from the uniform-neighbourhood
+// map or the edge average.
+template <typename T, typename ID>
+__device__ __forceinline__ T e_comp_at(const YeeArgs<T, ID> &a, const ID *__restrict__ emat, int c, int i, int j,
+                                       int k) {
+  const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
+  if (i >= nx || j >= ny || k >= nz) return T(0);
+  if ((c == 0 && (j == 0 || k == 0)) || (c == 1 && (i == 0 || k == 0)) || (c == 2 && (i == 0 || j == 0))) return T(0);
+  const int64_t nc = a.nc, plane = (int64_t)nx * ny, n = k * plane + (int64_t)j * nx + i;
+  auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+  const T *Hx = a.Hin, *Hy = a.Hin + nc, *Hz = a.Hin + 2 * nc;
+  const ID none = (ID)~(ID)0, mu = __ldg(emat + n);
+  T ca, cb, curl;
+  const ID *M = a.mat;
+  if (c == 0) {
+    curl = (__ldg(Hz + n) - __ldg(Hz + n - nx)) * ax(AX_RDD, nx + j) -
+           (__ldg(Hy + n) - __ldg(Hy + n - plane)) * ax(AX_RDD, nx + ny + k);
+    if (mu != none) { ca = __ldg(a.ctab + mu); cb = __ldg(a.ctab + a.nmat + mu); }
+    else e_coef(a, M[n - nx - plane], M[n - plane], M[n - nx], M[n], ax(AX_WLO, nx + j), ax(AX_WHI, nx + j),
+                ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+  } else if (c == 1) {
+    curl = (__ldg(Hx + n) - __ldg(Hx + n - plane)) * ax(AX_RDD, nx + ny + k) -
+           (__ldg(Hz + n) - __ldg(Hz + n - 1)) * ax(AX_RDD, i);
+    if (mu != none) { ca = __ldg(a.ctab + mu); cb = __ldg(a.ctab + a.nmat + mu); }
+    else e_coef(a, M[n - 1 - plane], M[n - plane], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i),
+                ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+  } else {
+    curl = (__ldg(Hy + n) - __ldg(Hy + n - 1)) * ax(AX_RDD, i) - (__ldg(Hx + n) - __ldg(Hx + n - nx)) * ax(AX_RDD, nx + j);
+    if (mu != none) { ca = __ldg(a.ctab + mu); cb = __ldg(a.ctab + a.nmat + mu); }
+    else e_coef(a, M[n - 1 - nx], M[n - nx], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i), ax(AX_WLO, nx + j),
+                ax(AX_WHI, nx + j), ca, cb);
+  }
+  return ca * __ldg(a.Ein + c * nc + n) + cb * curl;
+}
+
+template <typename T, typename ID, bool HOMOG_H, int VW>
+__global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+  wait_prior_grid();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = (blockIdx.x * LTX + tx) * VW, j = blockIdx.y * LTY + ty;
+  const int k0 = blockIdx.z * lz, k1 = min(a.nz, k0 + lz);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
+  const int64_t nc = a.nc, plane = (int64_t)nx * ny;
+  auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+  if (j >= ny) {  // warp-uniform
+    allow_next_grid();
+    return;
+  }
+  const bool live = i0 < nx;
+  const T *Hx = a.Hin, *Hy = a.Hin + nc, *Hz = a.Hin + 2 * nc;
+  const ID *M = a.mat;
+  const ID none = (ID)~(ID)0;
+  const T ryd = ax(AX_RDD, nx + j), wyl = ax(AX_WLO, nx + j), wyh = ax(AX_WHI, nx + j);
+  const T rdy = ax(AX_RD, nx + j);
+  T rxd[VW], rdx[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    rxd[e] = live ? ax(AX_RDD, i0 + e) : T(0);
+    rdx[e] = live ? ax(AX_RD, i0 + e) : T(0);
+  }
+  const T da0 = __ldg(a.ctab + 2 * a.nmat), db0 = __ldg(a.ctab + 3 * a.nmat);
+  // carried from plane k - 1: old H (own), new E (own, +x and +y neighbours)
+  T hx_p[VW], hy_p[VW], hz_p[VW], ex_p[VW], ey_p[VW], ez_p[VW], exy_p[VW], ezy_p[VW];
+  T eyx_p = T(0), ezx_p = T(0);
+#pragma unroll
+  for (int e = 0; e < VW; ++e) hx_p[e] = hy_p[e] = hz_p[e] = ex_p[e] = ey_p[e] = ez_p[e] = exy_p[e] = ezy_p[e] = T(0);
+  int64_t n = k0 * plane + (int64_t)j * nx + i0;
+  if (live && k0 > 0) {
+    ldv<VW, false>(hx_p, Hx + n - plane);
+    ldv<VW, false>(hy_p, Hy + n - plane);
+  }
+  for (int k = k0; k <= k1; ++k, n += plane) {
+    const bool top = k == k1;          // plane of the chunk above: Ex, Ey for H(k-1) only
+    const bool inbox = k < nz;
+    T hx[VW], hy[VW], hz[VW], hx_jm[VW], hz_jm[VW], ex[VW], ey[VW], ez[VW];
+    ID mu[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) hx[e] = hy[e] = hz[e] = hx_jm[e] = hz_jm[e] = ex[e] = ey[e] = ez[e] = T(0);
+    T hy_l = T(0), hz_l = T(0);
+    if (live && inbox) {
+      ldv<VW, false>(hx, Hx + n);
+      ldv<VW, false>(hy, Hy + n);
+      ldv<VW, false>(hz, Hz + n);
+      if (j > 0) {
+        ldv<VW, false>(hx_jm, Hx + n - nx);
+        ldv<VW, false>(hz_jm, Hz + n - nx);
+      }
+      ldv<VW, false>(ex, a.Ein + n);
+      ldv<VW, false>(ey, a.Ein + nc + n);
+      ldv<VW, false>(ez, a.Ein + 2 * nc + n);
+      ldids<VW>(mu, emat + n);
+      if (tx == 0 && i0 > 0) {
+        hy_l = __ldg(Hy + n - 1);
+        hz_l = __ldg(Hz + n - 1);
+      }
+    }
+    const T hy_s = __shfl_up_sync(0xffffffffu, hy[VW - 1], 1), hz_s = __shfl_up_sync(0xffffffffu, hz[VW - 1], 1);
+    if (tx > 0) { hy_l = hy_s; hz_l = hz_s; }
+    // E^{n+1}(k) on the own cells
+    T ox[VW], oy[VW], oz[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) ox[e] = oy[e] = oz[e] = T(0);
+    if (live && inbox) {
+      const T rzd = ax(AX_RDD, nx + ny + k);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int i = i0 + e;
+        const T hy_im = e == 0 ? hy_l : hy[e - 1], hz_im = e == 0 ? hz_l : hz[e - 1];
+        T cax, cbx, cay, cby, caz, cbz;
+        if (mu[e] != none) {
+          cax = cay = caz = __ldg(a.ctab + mu[e]);
+          cbx = cby = cbz = __ldg(a.ctab + a.nmat + mu[e]);
+        } else {
+          const int64_t c = n + e;
+          const T wxl = ax(AX_WLO, i), wxh = ax(AX_WHI, i);
+          const T wzl = ax(AX_WLO, nx + ny + k), wzh = ax(AX_WHI, nx + ny + k);
+          const ID m = M[c];
+          const ID m_i = i > 0 ? M[c - 1] : m, m_j = j > 0 ? M[c - nx] : m, m_k = k > 0 ? M[c - plane] : m;
+          const ID m_ij = (i > 0 && j > 0) ? M[c - 1 - nx] : m, m_ik = (i > 0 && k > 0) ? M[c - 1 - plane] : m;
+          const ID m_jk = (j > 0 && k > 0) ? M[c - nx - plane] : m;
+          e_coef(a, m_jk, m_k, m_j, m, wyl, wyh, wzl, wzh, cax, cbx);
+          e_coef(a, m_ik, m_k, m_i, m, wxl, wxh, wzl, wzh, cay, cby);
+          e_coef(a, m_ij, m_j, m_i, m, wxl, wxh, wyl, wyh, caz, cbz);
+        }
+        if (j == 0 || k == 0) cax = cbx = T(0);
+        if (i == 0 || k == 0) cay = cby = T(0);
+        if (i == 0 || j == 0) caz = cbz = T(0);
+        ox[e] = cax * ex[e] + cbx * ((hz[e] - hz_jm[e]) * ryd - (hy[e] - hy_p[e]) * rzd);
+        oy[e] = cay * ey[e] + cby * ((hx[e] - hx_p[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
+        oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
+      }
+      if (!top) {
+        stv<VW>(a.Eout + n, ox);
+        stv<VW>(a.Eout + nc + n, oy);
+        stv<VW>(a.Eout + 2 * nc + n, oz);
+      }
+    }
+    // neighbours' E^{n+1}(k) for H(k): +y row (recomputed), +x cell (next lane)
+    T exy[VW], ezy[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) exy[e] = ezy[e] = T(0);
+    T eyx = __shfl_down_sync(0xffffffffu, oy[0], 1), ezx = __shfl_down_sync(0xffffffffu, oz[0], 1);
+    if (!top) {
+      if (live && inbox) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          exy[e] = e_comp_at(a, emat, 0, i0 + e, j + 1, k);
+          ezy[e] = e_comp_at(a, emat, 2, i0 + e, j + 1, k);
+        }
+      }
+      if (tx == LTX - 1) {
+        eyx = live && inbox ? e_comp_at(a, emat, 1, i0 + VW, j, k) : T(0);
+        ezx = live && inbox ? e_comp_at(a, emat, 2, i0 + VW, j, k) : T(0);
+      }
+    }
+    // H^{n+3/2}(k - 1) from E^{n+1}(k - 1) and E^{n+1}(k)
+    if (k > k0 && live) {
+      const int kh = k - 1;
+      const int64_t nh = n - plane;
+      const T rdz = ax(AX_RD, nx + ny + kh);
+      T nhx[VW], nhy[VW], nhz[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int i = i0 + e;
+        T da[3] = {da0, da0, da0}, db[3] = {db0, db0, db0};
+        if (!HOMOG_H) {
+          const int64_t c = nh + e;
+          const ID m = M[c];
+          if (i > 0) h_coef(a, M[c - 1], m, ax(AX_WLO, i), ax(AX_WHI, i), da[0], db[0]);
+          if (j > 0) h_coef(a, M[c - nx], m, ax(AX_WLO, nx + j), ax(AX_WHI, nx + j), da[1], db[1]);
+          if (kh > 0) h_coef(a, M[c - plane], m, ax(AX_WLO, nx + ny + kh), ax(AX_WHI, nx + ny + kh), da[2], db[2]);
+        }
+        const T ey_ip = e == VW - 1 ? eyx_p : ey_p[e + 1], ez_ip = e == VW - 1 ? ezx_p : ez_p[e + 1];
+        const T hxv = da[0] * hx_p[e] - db[0] * ((ezy_p[e] - ez_p[e]) * rdy - (oy[e] - ey_p[e]) * rdz);
+        const T hyv = da[1] * hy_p[e] - db[1] * ((ox[e] - ex_p[e]) * rdz - (ez_ip - ez_p[e]) * rdx[e]);
+        const T hzv = da[2] * hz_p[e] - db[2] * ((ey_ip - ey_p[e]) * rdx[e] - (exy_p[e] - ex_p[e]) * rdy);
+        nhx[e] = i == 0 ? T(0) : hxv;
+        nhy[e] = j == 0 ? T(0) : hyv;
+        nhz[e] = kh == 0 ? T(0) : hzv;
+      }
+      stv<VW>(a.Hout + nh, nhx);
+      stv<VW>(a.Hout + nc + nh, nhy);
+      stv<VW>(a.Hout + 2 * nc + nh, nhz);
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      hx_p[e] = hx[e];
+      hy_p[e] = hy[e];
+      hz_p[e] = hz[e];
+      ex_p[e] = ox[e];
+      ey_p[e] = oy[e];
+      ez_p[e] = oz[e];
+      exy_p[e] = exy[e];
+      ezy_p[e] = ezy[e];
+    }
+    eyx_p = eyx;
+    ezx_p = ezx;
+  }
+  allow_next_grid();
+}
+
+// Sources after the fused pass: E^{n+1}_e += dE = -Cb w u on each source edge
+// and H^{n+3/2} -= Db (curlE dE) on the four H edges whose curl contains it.
+struct FlatPort {
+  int64_t cell;
+  int comp, port;
+  double w;
+};
+
+template <typename T, typename ID, bool HOMOG_H>
+__global__ void yee_march_src_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ src, int nsrc) {
+  wait_prior_grid();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nsrc) {
+    const FlatPort f = src[q];
+    const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
+    const int64_t nc = a.nc, plane = (int64_t)nx * ny, n = f.cell;
+    const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / plane);
+    auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+    const ID *M = a.mat;
+    T ca, cb = 0;
+    const int c = f.comp;
+    if (c == 0 && j > 0 && k > 0)
+      e_coef(a, M[n - nx - plane], M[n - plane], M[n - nx], M[n], ax(AX_WLO, nx + j), ax(AX_WHI, nx + j),
+             ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+    else if (c == 1 && i > 0 && k > 0)
+      e_coef(a, M[n - 1 - plane], M[n - plane], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i),
+             ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+    else if (c == 2 && i > 0 && j > 0)
+      e_coef(a, M[n - 1 - nx], M[n - nx], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i), ax(AX_WLO, nx + j),
+             ax(AX_WHI, nx + j), ca, cb);
+    const T dE = -cb * (T)f.w * a.u[f.port];
+    if (dE != T(0)) {
+      atomicAdd(&a.Eout[c * nc + n], dE);
+      // Db of H component hc at cell (ii, jj, kk), 0 where the update forces H to 0
+      auto dbh = [&](int hc, int ii, int jj, int kk) -> T {
+        if (ii < 0 || jj < 0 || kk < 0) return T(0);
+        if ((hc == 0 && ii == 0) || (hc == 1 && jj == 0) || (hc == 2 && kk == 0)) return T(0);
+        T da = __ldg(a.ctab + 2 * a.nmat), db = __ldg(a.ctab + 3 * a.nmat);
+        if (!HOMOG_H) {
+          const int64_t cc = kk * plane + (int64_t)jj * nx + ii;
+          const int idx = hc == 0 ? ii : (hc == 1 ? nx + jj : nx + ny + kk);
+          const int64_t lo = hc == 0 ? cc - 1 : (hc == 1 ? cc - nx : cc - plane);
+          h_coef(a, M[lo], M[cc], ax(AX_WLO, idx), ax(AX_WHI, idx), da, db);
+        }
+        return db;
+      };
+      auto addh = [&](int hc, int ii, int jj, int kk, T coef) {
+        const T db = dbh(hc, ii, jj, kk);
+        if (db != T(0)) atomicAdd(&a.Hout[hc * nc + kk * plane + (int64_t)jj * nx + ii], -db * coef * dE);
+      };
+      // (curl E)_hc at an H edge = sum of +-(1/d) E over its face; the terms of this E edge:
+      if (c == 0) {         // Ex(i,j,k): Hy(i,j,k) -1/dz_k, Hy(i,j,k-1) +1/dz_{k-1}, Hz(i,j,k) +1/dy_j, Hz(i,j-1,k) -1/dy_{j-1}
+        addh(1, i, j, k, -ax(AX_RD, nx + ny + k));
+        if (k > 0) addh(1, i, j, k - 1, ax(AX_RD, nx + ny + k - 1));
+        addh(2, i, j, k, ax(AX_RD, nx + j));
+        if (j > 0) addh(2, i, j - 1, k, -ax(AX_RD, nx + j - 1));
+      } else if (c == 1) {  // Ey(i,j,k): Hz(i,j,k) -1/dx_i, Hz(i-1,j,k) +1/dx_{i-1}, Hx(i,j,k) +1/dz_k, Hx(i,j,k-1) -1/dz_{k-1}
+        addh(2, i, j, k, -ax(AX_RD, i));
+        if (i > 0) addh(2, i - 1, j, k, ax(AX_RD, i - 1));
+        addh(0, i, j, k, ax(AX_RD, nx + ny + k));
+        if (k > 0) addh(0, i, j, k - 1, -ax(AX_RD, nx + ny + k - 1));
+      } else {              // Ez(i,j,k): Hx(i,j,k) -1/dy_j, Hx(i,j-1,k) +1/dy_{j-1}, Hy(i,j,k) +1/dx_i, Hy(i-1,j,k) -1/dx_{i-1}
+        addh(0, i, j, k, -ax(AX_RD, nx + j));
+        if (j > 0) addh(0, i, j - 1, k, ax(AX_RD, nx + j - 1));
+        addh(1, i, j, k, ax(AX_RD, i));
+        if (i > 0) addh(1, i - 1, j, k, -ax(AX_RD, i - 1));
+      }
+      (void)nz;
+    }
+  }
+  allow_next_grid();
+}
+
+// Probes of the final E^{n+1}.
+template <typename T, typename ID>
+__global__ void yee_march_prb_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ prb, int nprb) {
+  wait_prior_grid();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nprb) {
+    const FlatPort f = prb[q];
+    atomicAdd(&a.y[f.port], (T)f.w * a.Eout[f.comp * a.nc + f.cell]);
+  }
+  allow_next_grid();
+}
+
+static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
+  if (g->flat_ready) return FDTD_OK;
+  auto build = [&](const std::vector<HostPort> &ports, DevBuf &buf, int &count) -> fdtd_status {
+    std::vector<FlatPort> v;
+    for (size_t p = 0; p < ports.size(); ++p)
+      for (size_t e = 0; e < ports[p].cell.size(); ++e)
+        v.push_back(FlatPort{ports[p].cell[e], ports[p].comp, (int)p, ports[p].w[e]});
+    count = (int)v.size();
+    FDTD_CHECK(buf.alloc(std::max<size_t>(1, v.size()) * sizeof(FlatPort), s));
+    if (!v.empty())
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(FlatPort), cudaMemcpyHostToDevice, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    return FDTD_OK;
+  };
+  FDTD_CHECK(build(g->ports, g->flat_src, g->nflat_src));
+  FDTD_CHECK(build(g->probes, g->flat_prb, g->nflat_prb));
+  g->flat_ready = true;
+  return FDTD_OK;
+}
+
+template <typename T, typename ID, bool HH, int VW>
+static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  FDTD_CHECK(ensure_emat<ID>(g, s));
+  FDTD_CHECK(ensure_flat(g, s));
+  YeeArgs<T, ID> a = split_args<T, ID>(g);
+  a.u = static_cast<const T *>(u_row);
+  a.y = static_cast<T *>(y_row);
+  const int lz = std::min(g->nz, g->tune_lz > 0 ? g->tune_lz : env_int("FDTDMOR_LZ", 16));
+  const dim3 grid((g->nx + LTX * VW - 1) / (LTX * VW), (g->ny + LTY - 1) / LTY, (g->nz + lz - 1) / lz);
+  FDTD_CHECK_CUDA(launch_dependent(yee_march_kernel<T, ID, HH, VW>, grid, dim3(LTX, LTY), s, a, g->emat.as<ID>(), lz));
+  FDTD_CHECK(after_launch("yee_march_kernel"));
+  if (g->nflat_src) {
+    FDTD_CHECK_CUDA(launch_dependent(yee_march_src_kernel<T, ID, HH>, dim3((g->nflat_src + 127) / 128), dim3(128), s, a,
+                                     g->flat_src.as<const FlatPort>(), g->nflat_src));
+    FDTD_CHECK(after_launch("yee_march_src_kernel"));
+  }
+  if (g->nflat_prb) {
+    FDTD_CHECK_CUDA(launch_dependent(yee_march_prb_kernel<T, ID>, dim3((g->nflat_prb + 127) / 128), dim3(128), s, a,
+                                     g->flat_prb.as<const FlatPort>(), g->nflat_prb));
+    FDTD_CHECK(after_launch("yee_march_prb_kernel"));
+  }
+  return FDTD_OK;
+}
+
+template <typename T, typename ID, bool HH>
+static fdtd_status launch_march_t(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  if (yee_split_vw(g) == 2) return launch_march_v<T, ID, HH, 2>(g, u_row, y_row, s);
+  return launch_march_v<T, ID, HH, 1>(g, u_row, y_row, s);
+}
+
+fdtd_status launch_yee_march(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
+  if (g->prec == FDTD_F64) {
+    if (g->id_bytes == 1)
+      return g->homog_h ? launch_march_t<double, uint8_t, true>(g, u_row, y_row, s)
+                        : launch_march_t<double, uint8_t, false>(g, u_row, y_row, s);
+    return g->homog_h ? launch_march_t<double, uint16_t, true>(g, u_row, y_row, s)
+                      : launch_march_t<double, uint16_t, false>(g, u_row, y_row, s);
+  }
+  if (g->id_bytes == 1)
+    return g->homog_h ? launch_march_t<float, uint8_t, true>(g, u_row, y_row, s)
+                      : launch_march_t<float, uint8_t, false>(g, u_row, y_row, s);
+  return g->homog_h ? launch_march_t<float, uint16_t, true>(g, u_row, y_row, s)
+                    : launch_march_t<float, uint16_t, false>(g, u_row, y_row, s);
+}
+
+}  // namespace fdtdmor

@@ -269,7 +269,7 @@ class Grid:
         check(lib().fdtd_check(self.h, _stream_ptr(stream)))
 
     def set_kernel(self, kernel: str):
-        """Leap-frog kernel form: 'auto', 'persist', 'split', 'tma' or 'fused'."""
+        """Leap-frog kernel form: 'auto', 'persist', 'split', 'tma', 'fused' or 'march'."""
         check(lib().fdtd_grid_set_kernel(self.h, KERNELS[kernel]))
 
     def set_materials(self, eps_r, mu_r=None, sig_e=None, sig_m=None, pec=None, stream=None):
@@ -349,7 +349,7 @@ class Grid:
         check(lib().fdtd_fields_set(self.h, _dptr(f), _stream_ptr(stream)))
 
 
-KERNELS = {"auto": 0, "persist": 1, "split": 2, "tma": 3, "fused": 4}
+KERNELS = {"auto": 0, "persist": 1, "split": 2, "tma": 3, "fused": 4, "march": 5}
 
 MODEL_FIELDS = {"De": 0, "Dse": 1, "Dm": 2, "Dsm": 3, "K": 4, "Kp": 5, "BE": 6, "CE": 7, "sigma": 8}
 

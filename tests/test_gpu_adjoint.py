@@ -38,7 +38,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("kernel", ["split", "persist", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "persist", "fused", "march"])
 def test_adjoint_f64_matches_oracle(kernel):
     grid = ragged_grid(nx=13, ny=11, nz=9, seed=31)
     dt = 0.95 * yee.cfl_dt(grid)

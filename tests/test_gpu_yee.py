@@ -44,7 +44,8 @@ def test_cfl_matches_oracle():
         assert abs(g.cfl_dt() - yee.cfl_dt(grid)) <= 1e-15 * yee.cfl_dt(grid)
 
 
-KERNEL_CASES = [("persist", 41), ("split", 41), ("fused", 41), ("persist", 48), ("split", 48), ("tma", 48)]
+KERNEL_CASES = [("persist", 41), ("split", 41), ("fused", 41), ("march", 41), ("persist", 48), ("split", 48),
+                ("tma", 48), ("march", 48)]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -83,7 +84,7 @@ def test_config1_f64_full_run():
     assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
 
 
-@pytest.mark.parametrize("kernel", ["persist", "split", "fused"])
+@pytest.mark.parametrize("kernel", ["persist", "split", "fused", "march"])
 def test_state_continues_across_calls_and_host_variant(kernel):
     grid = ragged_grid(seed=7)
     dt = 0.9 * yee.cfl_dt(grid)
@@ -115,14 +116,14 @@ def test_kernel_forms_agree_and_persistent_chunks():
     dt = 0.97 * yee.cfl_dt(grid)
     u = drive(grid, dt, 8200)
     _, yo, fo = _run_oracle(grid, dt, u)
-    for kernel in ("persist", "split", "fused"):
+    for kernel in ("persist", "split", "fused", "march"):
         g, yg, fg = _run_gpu(grid, "f64", dt, u, kernel=kernel)
         g.check()
         assert np.max(np.abs(fg - fo)) <= 1e-8 * np.abs(fo).max(), kernel
         assert np.max(np.abs(yg - yo)) <= 1e-8 * np.abs(yo).max(), kernel
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "march"])
 def test_graph_replays_follow_parity_and_dt(kernel):
     """Runs long enough to be replayed from captured graphs: an odd-length
     call first (the next replays start from the other buffer), then a new dt
