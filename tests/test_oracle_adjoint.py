@@ -42,3 +42,36 @@ def test_adjoint_matches_central_differences():
         Lm = adjoint.loss_of_eps(lambda e: _grid_with_cell_eps(e, (n,)), em, dt, u)
         fd = (Lp - Lm) / (2 * h)
         assert abs(grad[c] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max())
+
+
+def test_reduced_model_gradient_matches_central_differences():
+    """Gradient of a probe loss of the reduced model with the projection V
+    frozen (D~eps = V1^T D_eps V1 rebuilt from the perturbed grid, same V1)
+    against central differences of that reduced run."""
+    from oracle import mor
+    n = 5
+    rng = np.random.default_rng(8)
+    eps = rng.uniform(1.0, 4.0, n ** 3)
+    g = _grid_with_cell_eps(eps, (n,))
+    s = yee.assemble(g)
+    dt0 = 0.99 * yee.cfl_dt(g)
+    basis = mor.sprim_basis(s, dt0, 12, 1, 1.1, 40e9)
+    red = mor.project(s, basis.V1, basis.V2)
+    T = 150
+    u = W.excitation(g, 60e9, 60e9, dt0, T)
+    y = mor.reduced_run(red, dt0, u)
+    L, dLdy = adjoint.probe_energy_loss(y, dt0)
+    G = adjoint.reduced_grad_De(red, dt0, u, dLdy)
+    grad = adjoint.reduced_grad_eps_cells(s, basis.V1, G)
+
+    def loss(e_cells):
+        s2 = yee.assemble(_grid_with_cell_eps(e_cells, (n,)))
+        red2 = mor.project(s2, basis.V1, basis.V2)
+        return adjoint.probe_energy_loss(mor.reduced_run(red2, dt0, u), dt0)[0]
+
+    for c in rng.choice(n ** 3, 6, replace=False):
+        h = 1e-6 * eps[c]
+        ep = eps.copy(); ep[c] += h
+        em = eps.copy(); em[c] -= h
+        fd = (loss(ep) - loss(em)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-5 * np.abs(grad).max(), (c, fd, grad[c])
