@@ -329,6 +329,19 @@ FDTD_API fdtd_status mor_model_get(const mor_model *model, int which, double *ho
                                    int *cols, fdtd_stream_t stream);
 FDTD_API fdtd_status mor_model_destroy(mor_model *model);
 
+/* A12 (reduced model) -- gradient of a probe loss of the reduced leap-frog
+ * (Eq. (R_and_Freduced) as prepared by mor_perturb) with respect to eps_r,
+ * with the projection V frozen (D~eps = V1^T D_eps V1 is the only reduced
+ * matrix that depends on eps; K~ as prepared is held fixed).  Runs nsteps
+ * steps from zero state with u (device [nsteps][m]) and the adjoint driven by
+ * dloss_dy (device [nsteps][p]); the model, basis and grid must belong
+ * together.  Outputs (any may be NULL): grad_eps_cell (device FP64 [nc]),
+ * grad_eps_mat (device FP64 [nmat]), grad_De (host FP64 [q1][q1] = dL/dD~eps).
+ * Synchronises the stream. */
+FDTD_API fdtd_status mor_gradient(mor_model *model, const mor_basis *basis, fdtd_grid *grid, int64_t nsteps,
+                         const void *u, const void *dloss_dy, double *grad_eps_cell, double *grad_eps_mat,
+                         double *grad_De, fdtd_stream_t stream);
+
 /* A9 -- relative L2 error ||y_red - y_ref[sub]|| / ||y_ref[sub]|| over the
  * common samples: y_red [n][p], y_ref rows offset + i*stride, i < n (device,
  * type prec).  *err receives the value (host).  Synchronises the stream. */

@@ -27,28 +27,12 @@
 
 #include "common.cuh"
 #include "grid_internal.cuh"
+#include "mor_internal.cuh"
 
 namespace fdtdmor {
 
 fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y, int reset_fields,
                     cudaStream_t s);
-
-// Edge volume V_e = L_e A~_e of component c at cell (i, j, k) from the axis
-// tables (1/primal spacing, 1/dual spacing); 0 for an edge on a wall.
-template <typename T>
-__device__ __forceinline__ double edge_volume(const T *__restrict__ ax, int nx, int ny, int nz, int c, int i, int j,
-                                              int k) {
-  const int ntot = nx + ny + nz;
-  const int idx[3] = {i, nx + j, nx + ny + k};
-  double v = 1.0 / (double)__ldg(ax + AX_RD * ntot + idx[c]);
-  for (int a = 0; a < 3; ++a) {
-    if (a == c) continue;
-    const double r = (double)__ldg(ax + AX_RDD * ntot + idx[a]);
-    if (r == 0.0) return 0.0;
-    v /= r;
-  }
-  return v;
-}
 
 // gseg[e] += -(V_e/dt) e^[e] (E1[e] - E0[e]) over the 3 nc E edges.
 template <typename T>
@@ -165,6 +149,25 @@ struct AdjointView {
 };
 
 template <typename T>
+static fdtd_status edges_to_cells_t(fdtd_grid *g, const double *gedge, double *gcell, double *gmat, cudaStream_t s) {
+  if (gmat) FDTD_CHECK_CUDA(cudaMemsetAsync(gmat, 0, (size_t)g->nmat * sizeof(double), s));
+  const int nb1 = (int)((g->nc + 255) / 256);
+  const T *ax = g->axis.as<T>();
+  if (g->id_bytes == 1)
+    adj_cell_kernel<T, uint8_t><<<nb1, 256, 0, s>>>(ax, g->nx, g->ny, g->nz, g->nc, gedge, g->mat.as<uint8_t>(), gcell,
+                                                    gmat);
+  else
+    adj_cell_kernel<T, uint16_t><<<nb1, 256, 0, s>>>(ax, g->nx, g->ny, g->nz, g->nc, gedge, g->mat.as<uint16_t>(),
+                                                     gcell, gmat);
+  return after_launch("adj_cell_kernel");
+}
+
+fdtd_status edges_to_cells(fdtd_grid *g, const double *gedge, double *gcell, double *gmat, cudaStream_t s) {
+  return g->prec == FDTD_F64 ? edges_to_cells_t<double>(g, gedge, gcell, gmat, s)
+                             : edges_to_cells_t<float>(g, gedge, gcell, gmat, s);
+}
+
+template <typename T>
 static fdtd_status adjoint_t(fdtd_grid *g, double dt, int64_t T_, const void *u, const void *dldy, int ncheck,
                              double *gcell, double *gmat, cudaStream_t s) {
   const int m = (int)g->ports.size(), p = (int)g->probes.size();
@@ -263,14 +266,7 @@ static fdtd_status adjoint_t(fdtd_grid *g, double dt, int64_t T_, const void *u,
     FDTD_CHECK(after_launch("adj_flush_kernel"));
   }
   FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)n6 * es, s));
-  if (gmat) FDTD_CHECK_CUDA(cudaMemsetAsync(gmat, 0, (size_t)g->nmat * sizeof(double), s));
-  if (g->id_bytes == 1)
-    adj_cell_kernel<T, uint8_t><<<nb1, th, 0, s>>>(ax, g->nx, g->ny, g->nz, nc, gedge.as<double>(),
-                                                   g->mat.as<uint8_t>(), gcell, gmat);
-  else
-    adj_cell_kernel<T, uint16_t><<<nb1, th, 0, s>>>(ax, g->nx, g->ny, g->nz, nc, gedge.as<double>(),
-                                                    g->mat.as<uint16_t>(), gcell, gmat);
-  FDTD_CHECK(after_launch("adj_cell_kernel"));
+  FDTD_CHECK(edges_to_cells(g, gedge.as<double>(), gcell, gmat, s));
   // the buffers are released on s after the last kernel that reads them
   return FDTD_OK;
 }

@@ -4,6 +4,13 @@
 
 namespace fdtdmor {
 
+// Gram products on the CUDA cores (mor_project.cu): G = A^T B, columns of
+// length n (stride n), FP64 out.
+fdtd_status gram_native(cudaStream_t s, int64_t n, const float *A, int M, const float *B, int N, double *out);
+fdtd_status gram_native(cudaStream_t s, int64_t n, const double *A, int M, const double *B, int N, double *out);
+// dL/d eps per edge (FP64, 3 nc) -> per cell and per material (adjoint.cu).
+fdtd_status edges_to_cells(fdtd_grid *g, const double *gedge, double *gcell, double *gmat, cudaStream_t s);
+
 // Tensor-core Gram products (gram_tc.cu): G = A^T diag(w) B, FP64 out.
 fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const float *src, int64_t ld, int ncols,
                       const float *w, void *dst);

@@ -185,6 +185,20 @@ static fdtd_status gram(cudaStream_t s, int64_t nrows, const T *A, int qa, const
   return after_launch("sum_slices_kernel");
 }
 
+fdtd_status gram_native(cudaStream_t s, int64_t n, const float *A, int M, const float *B, int N, double *out) {
+  DevBuf partial;
+  fdtd_status st = gram<float>(s, n, A, M, B, N, nullptr, partial, out);
+  partial.release(s);
+  return st;
+}
+
+fdtd_status gram_native(cudaStream_t s, int64_t n, const double *A, int M, const double *B, int N, double *out) {
+  DevBuf partial;
+  fdtd_status st = gram<double>(s, n, A, M, B, N, nullptr, partial, out);
+  partial.release(s);
+  return st;
+}
+
 template <typename T>
 static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, mor_model *M) {
   FDTD_CHECK(ensure_edge_props(g, s));

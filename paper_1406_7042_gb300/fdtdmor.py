@@ -124,6 +124,8 @@ _SIGS = [
     ("mor_model_get", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.c_void_p]),
     ("mor_model_destroy", C.c_int, [C.c_void_p]),
+    ("mor_gradient", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     ("mor_compare", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
                               C.POINTER(C.c_double), C.c_void_p]),
     ("mor_compare_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
@@ -435,6 +437,22 @@ class Model:
         check(lib().mor_run(self.h, n, _dptr(u) if self.grid.m else None, _dptr(y) if self.grid.p else None,
                             1 if reset else 0, _stream_ptr(stream)))
         return y
+
+    def gradient(self, basis: "Basis", u, dloss_dy, stream=None):
+        """dL/d eps_r of a probe loss of this reduced model with the basis
+        frozen (mor_gradient): returns (per-cell (nz, ny, nx) FP64 tensor,
+        per-material (nmat,) FP64 tensor, dL/dD~eps (q1, q1) numpy array)."""
+        import torch
+        s = self.grid.spec
+        n = int(u.shape[0] if self.grid.m else dloss_dy.shape[0])
+        gc = torch.empty((s.nz, s.ny, s.nx), dtype=torch.float64, device="cuda")
+        gm = torch.empty((s.nmat,), dtype=torch.float64, device="cuda")
+        q1 = basis.info()["q1"]
+        gd = np.zeros((q1, q1), np.float64)
+        check(lib().mor_gradient(self.h, basis.h, self.grid.h, n, _dptr(u) if self.grid.m else None,
+                                 _dptr(dloss_dy) if self.grid.p else None, _dptr(gc), _dptr(gm),
+                                 gd.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+        return gc, gm, gd
 
     def get(self, name: str, stream=None) -> np.ndarray:
         which = MODEL_FIELDS[name]

@@ -157,3 +157,50 @@ def test_metascreen_full_size_central_differences():
         fd.append((Ls[0] - Ls[1]) / (2 * h))
     fd = np.array(fd)
     assert _rel(gm[pix], fd) <= 5e-2, (gm[pix], fd)
+
+
+def _oracle_basis_from_gpu(sys, basis, spec):
+    """The GPU basis columns in the oracle's unknown order (live E / H edges)."""
+    nz, ny, nx = spec.nz, spec.ny, spec.nx
+    zero = np.zeros((nz, ny, nx))
+    out = []
+    for which, keys in ((1, ("Ex", "Ey", "Ez")), (2, ("Hx", "Hy", "Hz"))):
+        V = basis.V(which).double().cpu().numpy().reshape(-1, 3, nz, ny, nx)
+        cols = []
+        for col in V:
+            d = {k: zero for k in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")}
+            d.update({keys[c]: col[c] for c in range(3)})
+            x = sys.from_arrays(d)
+            cols.append(x[:sys.Ne] if which == 1 else x[sys.Ne:])
+        out.append(np.stack(cols, axis=1))
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 2e-3)])
+def test_reduced_model_gradient_matches_oracle(prec, tol):
+    """mor_gradient (basis frozen) against the oracle's reduced-model adjoint
+    on the same basis: dL/dD~eps and the per-cell gradient."""
+    from oracle import mor
+    g = ragged_grid(nx=14, ny=10, nz=9, seed=36)
+    grid = F.Grid(g, prec)
+    dt0 = 0.99 * grid.cfl_dt()
+    basis = F.Basis(grid, 12, dt0, L=1, M=1.1, fmax=40e9, tol=1e-10 if prec == "f64" else 1e-6, defl_tol=1e-6)
+    model = F.Model(grid, basis)
+    assert model.perturb(dt0) == 0
+    T = 150
+    u = drive(g, dt0, T)
+    ut = torch.tensor(u, dtype=grid.dtype, device="cuda")
+    y = model.run(ut)
+    gy = (2.0 * dt0) * y
+    gc, gm, gD = model.gradient(basis, ut, gy)
+    sys = yee.assemble(g)
+    V1, V2 = _oracle_basis_from_gpu(sys, basis, g)
+    red = mor.project(sys, V1, V2)
+    yo = mor.reduced_run(red, dt0, u)
+    Go = oadj.reduced_grad_De(red, dt0, u, 2.0 * dt0 * yo)
+    gco = oadj.reduced_grad_eps_cells(sys, V1, Go)
+    assert _rel(gD, Go) <= tol
+    assert np.max(np.abs(gc.cpu().numpy().ravel() - gco)) <= tol * np.abs(gco).max()
+    ids = g.mat_id.ravel().astype(np.int64)
+    gm_ref = np.bincount(ids, weights=gc.cpu().numpy().ravel(), minlength=g.nmat)
+    assert np.allclose(gm.cpu().numpy(), gm_ref, rtol=1e-9, atol=1e-12 * np.abs(gm_ref).max())
