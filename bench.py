@@ -280,6 +280,7 @@ def run_ours(args):
     if rank == 0 and args.tensor:
         line["tensor_gram"] = tensor_gram_measure(F, peaks)
         line["precision_study"] = precision_study(F, W)
+        line["precision_study_absorbing"] = precision_study(F, W, absorbing=True)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl, dt0, args.cpu_seconds)
     if rank == 0:
@@ -389,12 +390,13 @@ def tensor_gram_measure(F, peaks, n=786432, q=200, reps=5):
     return out
 
 
-def precision_study(F, W):
+def precision_study(F, W, absorbing=False):
     """The 100x50x24 microstrip (q = 100): basis and projection with FP32,
     TF32 and BF16 Gram-Schmidt products; reduced-model probe error at
-    s = 0.99 against the FP64 full-order run of the same grid."""
+    s = 0.99 against the FP64 full-order run of the same grid (PEC box, or
+    with the paper's matched absorber on five faces)."""
     import torch
-    wl = W.config4(downscale=True)
+    wl = W.config4(downscale=True, absorbing=absorbing)
     g = wl.grid
     ref = F.Grid(g, "f64")
     dt0 = wl.s_ref * ref.cfl_dt()
@@ -403,14 +405,20 @@ def precision_study(F, W):
     yref = ref.step(dt0, u64, reset=True)
     grid = F.Grid(g, "f32")
     u32 = u64.float()
-    out = {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "q": wl.q, "steps": n}
+    out = {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "steps": n}
     yfd = grid.step(dt0, u32, reset=True)
     out["fdtd_f32_err"] = round(F.compare(yfd, yref.float(), 1, 0), 8)
     y_native = None
+    # absorbing structure: radius of the expansion arc M = 1 + pi fmax dt0 and
+    # q = 200 (measured: 3e-5 probe error at s = 0.99; the paper's M = 1.1
+    # gives 0.24 at q = 100 here)
+    M = 1.0 + math.pi * wl.fmax * dt0 if absorbing else wl.M
+    q = 200 if absorbing else wl.q
+    out["M"], out["q"] = round(M, 5), q
     for orth in ("native", "tf32", "bf16"):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        basis = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=1e-5, defl_tol=1e-5, orth=orth, allow_noconv=True)
+        basis = F.Basis(grid, q, dt0, wl.L, M, wl.fmax, tol=1e-5, defl_tol=1e-5, orth=orth, allow_noconv=True)
         model = F.Model(grid, basis)
         b.record()
         torch.cuda.synchronize()
@@ -564,7 +572,8 @@ def main():
     if args.only_tensor:
         from paper_1406_7042_gb300 import fdtdmor as F
         from paper_1406_7042_gb300 import workloads as W
-        print(json.dumps({"tensor_gram": tensor_gram_measure(F, _peaks()), "precision_study": precision_study(F, W)}))
+        print(json.dumps({"tensor_gram": tensor_gram_measure(F, _peaks()), "precision_study": precision_study(F, W),
+                          "precision_study_absorbing": precision_study(F, W, absorbing=True)}))
         return 0
     if args.only_batch:
         from paper_1406_7042_gb300 import fdtdmor as F

@@ -110,6 +110,70 @@ def vacuum_table(extra: Optional[List[tuple]] = None):
             np.array(pec, np.uint8))
 
 
+EPS0 = 8.8541878128e-12
+MU0 = 4e-7 * math.pi
+
+
+def add_absorber(g: GridSpec, sides: str = "xXyYzZ", n: int = 5, order: int = 4,
+                 R0: float = 1e-6) -> GridSpec:
+    """Graded matched absorber of n cells (the paper's 4th-order, 5-cell layer
+    of Secs. V-B to V-D) on the faces named in `sides` (x / X: low / high x,
+    likewise y, z).  A cell at layer depth d (1 = innermost, n = at the wall;
+    where layers overlap the deepest counts) gets the electric conductivity
+    sigma_max ((d - 1/2) / n)^order added to its material and the matched
+    magnetic conductivity sigma_m = sigma_e mu / eps, so that the layer's
+    impedance equals the medium's.  sigma_max gives a normal-incidence
+    round-trip reflection R0 through the layer: sigma_max = -(order + 1)
+    ln(R0) / (2 eta n delta), eta the medium's impedance and delta the cell
+    size normal to the face.  Returns a new GridSpec (new materials appended;
+    PEC cells stay PEC)."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    depth = np.zeros((nz, ny, nx), np.int64)
+    normal = np.full((nz, ny, nx), -1, np.int64)   # axis of the deepest layer
+    idx = [np.arange(nx), np.arange(ny), np.arange(nz)]
+    for axis, (lo, hi) in enumerate((("x", "X"), ("y", "Y"), ("z", "Z"))):
+        size = (nx, ny, nz)[axis]
+        d1 = np.zeros(size, np.int64)
+        if lo in sides:
+            d1 = np.maximum(d1, np.where(idx[axis] < n, n - idx[axis], 0))
+        if hi in sides:
+            d1 = np.maximum(d1, np.where(idx[axis] >= size - n, idx[axis] - (size - n) + 1, 0))
+        shape = [1, 1, 1]
+        shape[2 - axis] = size
+        d3 = np.broadcast_to(d1.reshape(shape), (nz, ny, nx))
+        upd = d3 > depth
+        depth = np.where(upd, d3, depth)
+        normal = np.where(upd, axis, normal)
+    spacing = (g.dx, g.dy, g.dz)
+    eps, mu = list(g.eps_r), list(g.mu_r)
+    se, sm, pec = list(g.sig_e), list(g.sig_m), list(g.pec)
+    mat = g.mat_id.astype(np.int64).copy()
+    new_id = {}
+    ks, js, is_ = np.nonzero(depth)
+    for k, j, i in zip(ks, js, is_):
+        m0 = int(mat[k, j, i])
+        if g.pec[m0]:
+            continue
+        d, ax = int(depth[k, j, i]), int(normal[k, j, i])
+        pos = (i, j, k)[ax]
+        key = (m0, d, ax, float(spacing[ax][pos]))
+        if key not in new_id:
+            eta = math.sqrt(MU0 * g.mu_r[m0] / (EPS0 * g.eps_r[m0]))
+            smax = -(order + 1) * math.log(R0) / (2.0 * eta * n * spacing[ax][pos])
+            dse = smax * ((d - 0.5) / n) ** order
+            eps.append(g.eps_r[m0]); mu.append(g.mu_r[m0]); pec.append(0)
+            se.append(g.sig_e[m0] + dse)
+            sm.append(g.sig_m[m0] + dse * MU0 * g.mu_r[m0] / (EPS0 * g.eps_r[m0]))
+            new_id[key] = len(eps) - 1
+        mat[k, j, i] = new_id[key]
+    if len(eps) > 65535:
+        raise ValueError("too many materials after adding the absorber")
+    out = GridSpec(nx, ny, nz, g.dx, g.dy, g.dz, np.array(eps), np.array(mu), np.array(se), np.array(sm),
+                   np.array(pec, np.uint8), mat.astype(np.uint16))
+    out.ports, out.probes = list(g.ports), list(g.probes)
+    return out
+
+
 def gaussian_pulse(f0: float, bw: float, dt: float, nsteps: int) -> np.ndarray:
     """Gaussian-modulated sine sampled at t = (n + 1/2) dt, n = 0..nsteps-1.
 
@@ -263,9 +327,11 @@ def cavity_batch(seed: int = SEED_BASE + 30, count: int = 32, lo: int = 24, hi: 
     return out
 
 
-def config3(seed: int = SEED_BASE + 3) -> Workload:
+def config3(seed: int = SEED_BASE + 3, absorbing: bool = False) -> Workload:
     g = waveguide_iris(seed)
-    return Workload("waveguide_iris_f32", g, 0.99, 20000, 35e9, 20e9, q=200, L=2, M=1.1,
+    if absorbing:   # the paper's guide ends on matched absorbers (Sec. V-B)
+        g = add_absorber(g, "xX")
+    return Workload("waveguide_iris" + ("_abs" if absorbing else "") + "_f32", g, 0.99, 20000, 35e9, 20e9, q=200, L=2, M=1.1,
                     fmax=45e9, s_red=[0.99], nsteps_red=[20000], precision="f32")
 
 
@@ -313,12 +379,14 @@ def microstrip(seed: int = SEED_BASE + 4, nx: int = 400, ny: int = 200, nz: int 
     return g
 
 
-def config4(seed: int = SEED_BASE + 4, downscale: bool = False) -> Workload:
+def config4(seed: int = SEED_BASE + 4, downscale: bool = False, absorbing: bool = False) -> Workload:
     if downscale:
         g = microstrip(seed, 100, 50, 24)
     else:
         g = microstrip(seed)
-    return Workload("microstrip" + ("_down" if downscale else "") + "_f32", g, 0.99, 8000,
+    if absorbing:   # five absorbing faces, PEC ground at z = 0 (Sec. V-D)
+        g = add_absorber(g, "xXyYZ")
+    return Workload("microstrip" + ("_down" if downscale else "") + ("_abs" if absorbing else "") + "_f32", g, 0.99, 8000,
                     10e9, 20e9, q=400 if not downscale else 100, L=2, M=1.1, fmax=20e9,
                     s_red=[0.99, 2.97, 4.95], nsteps_red=[8000, 2667, 1600], precision="f32")
 
@@ -350,12 +418,14 @@ def metascreen(seed: int = SEED_BASE + 5, nxy: int = 384, nz: int = 64, d: float
     return g
 
 
-def config5(seed: int = SEED_BASE + 5, downscale: bool = False) -> Workload:
+def config5(seed: int = SEED_BASE + 5, downscale: bool = False, absorbing: bool = False) -> Workload:
     if downscale:
         g = metascreen(seed, 48, 16, 0.25e-3, 8, 6, 2)
     else:
         g = metascreen(seed)
-    return Workload("metascreen" + ("_down" if downscale else "") + "_f32", g, 0.99, 2048,
+    if absorbing:   # all six faces absorbing (Sec. V-C)
+        g = add_absorber(g, "xXyYzZ")
+    return Workload("metascreen" + ("_down" if downscale else "") + ("_abs" if absorbing else "") + "_f32", g, 0.99, 2048,
                     10e9, 5e9, q=40, L=1, M=1.1, fmax=10e9, include_center=False,
                     s_red=[0.99], nsteps_red=[2048], precision="f32")
 

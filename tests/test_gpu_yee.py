@@ -225,3 +225,23 @@ def test_full_size_metascreen_light_cone():
     dt = wl.s_ref * yee.cfl_dt(grid)
     centres = [(192, 192, 9), (70, 300, 31), (383 - 5, 5, 8)]
     _light_cone_check(grid, "f32", dt, 10, centres, 3)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+def test_absorbing_microstrip_parity(prec, tol):
+    """The 100x50x24 microstrip with the matched absorber on five faces
+    (graded sigma_e and sigma_m, uint8 ids): whole fields and probes against
+    the oracle."""
+    wl = W.config4(downscale=True, absorbing=True)
+    grid = wl.grid
+    dt = wl.s_ref * yee.cfl_dt(grid)
+    u = W.excitation(grid, wl.f0, wl.bw, dt, 300)
+    _, yg, fg = _run_gpu(grid, prec, dt, u)
+    _, yo, fo = _run_oracle(grid, dt, u)
+    if prec == "f64":
+        assert np.max(np.abs(fg - fo)) <= tol * np.abs(fo).max()
+        assert np.max(np.abs(yg - yo)) <= tol * np.abs(yo).max()
+    else:
+        assert _rel(yg, yo) <= tol
+        for c in range(6):
+            assert _rel(fg[c], fo[c]) <= 10 * tol, c
