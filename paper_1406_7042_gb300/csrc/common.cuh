@@ -135,6 +135,7 @@ struct fdtd_grid {
   fdtdmor::DevBuf gsync;        // ticket and per-slab completion counters of the dataflow kernel
   int kernel = 0;               // fdtd_kernel chosen by fdtd_grid_set_kernel (0 = automatic)
   int tune_vw = 0, tune_lz = 0; // split-kernel tile: x cells per thread, z planes per thread (0 = heuristic)
+  int tune_slab = 0;            // split-kernel z slab per launch pair (0 = the whole grid)
   fdtdmor::DevBuf flat_src, flat_prb;  // flat (cell, comp, port, w) lists of the fused z-march form
   int nflat_src = 0, nflat_prb = 0;
   bool flat_ready = false;

@@ -26,18 +26,19 @@
 namespace fdtdmor {
 
 template <typename T, typename ID, int VW>
-__global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 3 : 4) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+__global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 3 : 4) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
+                                                                        int kbase, int kend) {
   wait_prior_grid();
-  const int k0 = blockIdx.z * lz;
-  e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+  const int k0 = kbase + blockIdx.z * lz;
+  e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(kend, k0 + lz));
   allow_next_grid();
 }
 
 template <typename T, typename ID, bool HOMOG_H, int VW>
-__global__ void __launch_bounds__(LTX *LTY) yee_h_kernel(YeeArgs<T, ID> a, int lz) {
+__global__ void __launch_bounds__(LTX *LTY) yee_h_kernel(YeeArgs<T, ID> a, int lz, int kbase, int kend) {
   wait_prior_grid();
-  const int k0 = blockIdx.z * lz;
-  h_unit<T, ID, HOMOG_H, false, VW>(a, blockIdx.x, blockIdx.y, k0, min(a.nz, k0 + lz));
+  const int k0 = kbase + blockIdx.z * lz;
+  h_unit<T, ID, HOMOG_H, false, VW>(a, blockIdx.x, blockIdx.y, k0, min(kend, k0 + lz));
   allow_next_grid();
 }
 
@@ -165,12 +166,32 @@ static fdtd_status launch_split_v(fdtd_grid *g, const void *u_row, void *y_row, 
   a.u = static_cast<const T *>(u_row);
   a.y = static_cast<T *>(y_row);
   const int lz = yee_split_lz(g);
-  const dim3 grid(g->lists.ntx, g->lists.nty, (g->nz + lz - 1) / lz), block(LTX, LTY);
+  // z slabs ordered E(0), E(1), H(0), E(2), H(1), ...: H of slab s reads the
+  // E^{n+1} and H^{n+1/2} of its slab soon after E(s) and E(s + 1) touched
+  // them, while they are still in L2 (the kernels are out of place, so any
+  // order with H(s) after E(s) and E(s + 1) is exact)
+  const int slab = std::max(lz, std::min(g->nz, g->tune_slab > 0 ? g->tune_slab : env_int("FDTDMOR_SLAB", g->nz)));
+  const int nslab = (g->nz + slab - 1) / slab;
+  const dim3 block(LTX, LTY);
   const ID *emat = g->emat.as<ID>();
-  FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW>, grid, block, s, a, emat, lz));
-  FDTD_CHECK(after_launch("yee_e_kernel"));
-  FDTD_CHECK_CUDA(launch_dependent(yee_h_kernel<T, ID, HH, VW>, grid, block, s, a, lz));
-  return after_launch("yee_h_kernel");
+  auto E = [&](int q) -> fdtd_status {
+    const int kb = q * slab, ke = std::min(g->nz, kb + slab);
+    const dim3 grid(g->lists.ntx, g->lists.nty, (ke - kb + lz - 1) / lz);
+    FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW>, grid, block, s, a, emat, lz, kb, ke));
+    return after_launch("yee_e_kernel");
+  };
+  auto H = [&](int q) -> fdtd_status {
+    const int kb = q * slab, ke = std::min(g->nz, kb + slab);
+    const dim3 grid(g->lists.ntx, g->lists.nty, (ke - kb + lz - 1) / lz);
+    FDTD_CHECK_CUDA(launch_dependent(yee_h_kernel<T, ID, HH, VW>, grid, block, s, a, lz, kb, ke));
+    return after_launch("yee_h_kernel");
+  };
+  FDTD_CHECK(E(0));
+  for (int q = 1; q < nslab; ++q) {
+    FDTD_CHECK(E(q));
+    FDTD_CHECK(H(q - 1));
+  }
+  return H(nslab - 1);
 }
 
 template <typename T, typename ID, bool HH>
