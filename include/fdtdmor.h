@@ -213,6 +213,23 @@ FDTD_API fdtd_status fdtd_edge_props_get(fdtd_grid *grid, void *dst, fdtd_stream
 FDTD_API fdtd_status fdtd_adjoint(fdtd_grid *grid, double dt, int64_t nsteps, const void *u, const void *dloss_dy,
                          int ncheckpoints, double *grad_eps_cell, double *grad_eps_mat, fdtd_stream_t stream);
 
+/* NEXT-2 -- frequency-domain post-processing (the spectra the paper reads
+ * resonances from, Sec. V-A, and S-parameters from, Sec. V-D).
+ * fdtd_dft: Y_q(f) = sum_n w_n y^n_q exp(-j 2 pi f t_n) dt, t_n = (n + 1) dt
+ * (row n of y samples E^{n+1}), w_n = sin^2(pi (n + 1/2) / nsteps) when
+ * hann != 0, else 1.  y: device [nsteps][p] of type prec; freqs: host [nf]
+ * (Hz); out: host [p][nf][2] (re, im), FP64.  Synchronises the stream. */
+FDTD_API fdtd_status fdtd_dft(const void *y, int64_t nsteps, int p, fdtd_prec prec, double dt, int nf,
+                     const double *freqs, int hann, double *out, fdtd_stream_t stream);
+
+/* Resonances: the up to npk largest local maxima of sum_q |Y_q(f)| on nf
+ * uniform frequencies in [fmin, fmax] (maxima below rel_floor x the largest
+ * are dropped), each refined to the vertex of the parabola through its three
+ * samples; returned in ascending order in peaks_hz (host), count in *nfound. */
+FDTD_API fdtd_status fdtd_resonances(const void *y, int64_t nsteps, int p, fdtd_prec prec, double dt, double fmin,
+                            double fmax, int nf, int hann, double rel_floor, int npk, double *peaks_hz,
+                            int *nfound, fdtd_stream_t stream);
+
 /* Kernel launches issued by the calling thread since the last reset (for
  * launch accounting).  fdtd_launch_count(1) returns the count and resets it. */
 FDTD_API int64_t fdtd_launch_count(int reset);

@@ -98,6 +98,11 @@ _SIGS = [
     ("fdtd_launch_count", C.c_int64, [C.c_int]),
     ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("fdtd_dft", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                           C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    ("fdtd_resonances", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                  C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                  C.c_void_p]),
     ("fdtd_grid_set_kernel", C.c_int, [C.c_void_p, C.c_int]),
     ("fdtd_grid_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.c_void_p]),
@@ -507,6 +512,33 @@ def schur_apply(grid: "Grid", dt0: float, z, x, out=None, stream=None):
         out = torch.empty_like(x)
     check(lib().mor_schur_apply(grid.h, float(dt0), int(zz.size), zarr, _dptr(x), _dptr(out), _stream_ptr(stream)))
     return out
+
+
+def dft(y, dt: float, freqs, hann: bool = False, stream=None) -> np.ndarray:
+    """(p, nf) complex spectra of the probe waveforms y (nsteps, p) (fdtd_dft)."""
+    import torch
+    y = y.contiguous()
+    f = np.ascontiguousarray(np.asarray(freqs, np.float64))
+    out = np.zeros((y.shape[1], f.size, 2), np.float64)
+    prec = FDTD_F64 if y.dtype == torch.float64 else FDTD_F32
+    check(lib().fdtd_dft(_dptr(y), int(y.shape[0]), int(y.shape[1]), prec, float(dt), int(f.size),
+                         f.ctypes.data_as(C.POINTER(C.c_double)), 1 if hann else 0,
+                         out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def resonances(y, dt: float, fmin: float, fmax: float, nf: int = 4000, hann: bool = True, rel_floor: float = 0.05,
+               npk: int = 16, stream=None) -> np.ndarray:
+    """Resonance frequencies (Hz) read off the summed probe spectra (fdtd_resonances)."""
+    import torch
+    y = y.contiguous()
+    pk = np.zeros(npk, np.float64)
+    nfound = C.c_int()
+    prec = FDTD_F64 if y.dtype == torch.float64 else FDTD_F32
+    check(lib().fdtd_resonances(_dptr(y), int(y.shape[0]), int(y.shape[1]), prec, float(dt), float(fmin),
+                                float(fmax), int(nf), 1 if hann else 0, float(rel_floor), int(npk),
+                                pk.ctypes.data_as(C.POINTER(C.c_double)), C.byref(nfound), _stream_ptr(stream)))
+    return pk[:nfound.value]
 
 
 def compare(y_red, y_ref, stride: int, offset: int, stream=None) -> float:
