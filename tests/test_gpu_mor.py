@@ -320,3 +320,31 @@ def test_tensor_core_gram_schmidt_basis(orth, ortho_tol, span_tol):
         # same subspaces, possibly different bases: compare invariants
         sa, sb = np.linalg.svd(a, compute_uv=False), np.linalg.svd(b, compute_uv=False)
         assert np.max(np.abs(sa - sb)) <= 10 * span_tol * sa.max(), name
+
+
+def test_full_size_bench_workload_properties():
+    """The 64^3 graded cavity at full size in the bench's launch configuration
+    (FP32, BiCGSTAB, M = 1.0077), with a small order: orthonormal basis,
+    symmetric positive definite D~eps and D~mu, and after the perturbation at
+    20x CFL a reduced step matrix with no eigenvalue outside the unit circle
+    (Sec. III-A), checked in FP64 on the host from the projected matrices."""
+    from oracle import mor
+    wl = W.config2()
+    grid = F.Grid(wl.grid, "f32")
+    dt0 = wl.s_ref * grid.cfl_dt()
+    b = F.Basis(grid, 20, dt0, wl.L, wl.M, wl.fmax, tol=1e-4, defl_tol=1e-5, allow_noconv=True)
+    for which in (1, 2):
+        V = b.V(which).double()
+        eye = torch.eye(V.shape[0], dtype=torch.float64, device="cuda")
+        assert float((V @ V.T - eye).abs().max()) <= 1e-4
+    m = F.Model(grid, b)
+    De, Dm = m.get("De"), m.get("Dm")
+    for D in (De, Dm):
+        assert np.allclose(D, D.T, rtol=1e-6, atol=1e-9 * np.abs(D).max())
+        assert np.linalg.eigvalsh(0.5 * (D + D.T)).min() > 0
+    dt = wl.s_red[0] / wl.s_ref * dt0
+    m.perturb(dt)
+    red = mor.Reduced(De, m.get("Dse"), Dm, m.get("Dsm"), m.get("Kp"), m.get("BE"),
+                      np.zeros((Dm.shape[0], m.get("BE").shape[1])), m.get("CE"))
+    lam = np.abs(np.linalg.eigvals(mor.reduced_amplification(red, dt)))
+    assert lam.max() <= 1.0 + 1e-6
