@@ -119,19 +119,22 @@ FDTD_API fdtd_status fdtd_grid_set_materials(fdtd_grid *grid, int nmat, const do
 FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
 
 /* Kernel form of the leap-frog (A2).  All forms compute the same update.
- * AUTO: SPLIT.  PERSIST: one launch runs up to 8192 steps in place; its CTAs
- * take (step, half step, z slab, tile) work units in order from a counter and
- * wait (bounded) only for the slabs a unit depends on, so the E and H halves of
- * a slab meet in L2.  SPLIT: an E launch and an H launch per step, each thread
- * updating 4 (FP32) or 2 (FP64) consecutive x cells with vector loads when nx
- * allows.  TMA: one
- * fused launch per step staging planes through shared memory with the tensor
+ * AUTO: MARCH on FP32 grids of at least 2^22 cells whose nx is a multiple
+ * of 4 and at least 256, SPLIT otherwise.  PERSIST: one launch runs up to
+ * 8192 steps in place; its CTAs take (step, half step, z slab, tile) work
+ * units in order from a counter and wait (bounded) only for the slabs a unit
+ * depends on, so the E and H halves of a slab meet in L2.  SPLIT: an E launch
+ * and an H launch per step, each thread updating 4 (FP32) or 2 (FP64)
+ * consecutive x cells with vector loads when nx allows.  TMA: one fused
+ * launch per step staging planes through shared memory with the tensor
  * memory accelerator (needs nx a multiple of 16 for uint8 ids, 8 for uint16).
  * FUSED: one fused launch per step with plain loads into shared memory.
- * MARCH: one fused launch per step without block barriers: each thread
- * marches z, updating H one plane behind E and recomputing the two
- * neighbouring E values its H update needs; sources and probes follow in two
- * small launches (the step is linear). */
+ * MARCH: one fused pass over memory per step: a CTA marches z over a tile of
+ * 7 rows, each thread updating VW consecutive x cells (4 in FP32 on wide
+ * grids) with H one plane behind E; the rows exchange E through shared memory
+ * (one barrier per plane) and the tile's first row above and +x column are
+ * recomputed; sources and probes follow in two small launches (the step is
+ * linear). */
 typedef enum {
   FDTD_KERNEL_AUTO = 0,
   FDTD_KERNEL_PERSIST = 1,

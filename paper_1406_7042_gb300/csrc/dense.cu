@@ -145,9 +145,13 @@ __global__ void __launch_bounds__(256) jacobi_svd_kernel(double *Mc, int m, int 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (al > 0 && be > 0 && fabs(ga) > tol * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        // (sqrt(al) sqrt(be): the product al * be may underflow for columns
+        // in the null space)
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        // a rotation by an angle below rounding changes nothing: such a pair
+        // counts as orthogonal, so noise-level columns cannot stall the sweeps
+        if (al > 0 && be > 0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(t) > 1e-15) {
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
           for (int r = lane; r < m; r += 32) {
             const double x = Mc[(size_t)a * m + r], y = Mc[(size_t)b * m + r];

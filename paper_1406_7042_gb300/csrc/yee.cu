@@ -296,7 +296,7 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
                       (uint64_t)(uintptr_t)g->emat.ptr,
                       (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),
                       (uint64_t)g->lists.tx << 32 | (uint64_t)g->lists.ty,
-                      (uint64_t)(split ? yee_split_vw(g) : 0) << 32 | (uint64_t)(split ? yee_split_lz(g) : 0) |
+                      (uint64_t)(split ? yee_split_vw(g) + 8 * yee_march_vw(g) : 0) << 32 | (uint64_t)(split ? yee_split_lz(g) : 0) |
                           (uint64_t)(getenv("FDTDMOR_SLAB") ? atoi(getenv("FDTDMOR_SLAB")) : g->tune_slab) << 16,
                       (uint64_t)(uintptr_t)g->fields[0].ptr ^ ((uint64_t)(uintptr_t)g->fields[1].ptr << 1)};
   const int c = g->cur;
@@ -363,10 +363,14 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
          : v == "march" ? FDTD_KERNEL_MARCH : kind;
   }
   if (kind == FDTD_KERNEL_TMA && !yee_tma_eligible(g)) kind = FDTD_KERNEL_FUSED;
-  if (kind == FDTD_KERNEL_AUTO) kind = FDTD_KERNEL_SPLIT;
+  // AUTO: the fused one-pass form where its 128-cell FP32 tiles fill the grid
+  // and there are enough of them to fill the GPU, else the split pair
+  if (kind == FDTD_KERNEL_AUTO)
+    kind = (yee_march_vw(g) == 4 && g->nc >= ((int64_t)1 << 22)) ? FDTD_KERNEL_MARCH : FDTD_KERNEL_SPLIT;
   int ttx = YTX, tty = YTY;
   if (kind == FDTD_KERNEL_TMA) yee_tma_tile(&ttx, &tty);
-  if (kind == FDTD_KERNEL_PERSIST || kind == FDTD_KERNEL_SPLIT || kind == FDTD_KERNEL_MARCH) ttx = 32 * yee_split_vw(g);
+  if (kind == FDTD_KERNEL_PERSIST || kind == FDTD_KERNEL_SPLIT) ttx = 32 * yee_split_vw(g);
+  if (kind == FDTD_KERNEL_MARCH) ttx = 32 * yee_march_vw(g);
   FDTD_CHECK(build_tile_lists(g, ttx, tty, s));
   if (reset_fields) {
     FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)6 * g->nc * g->elem, s));

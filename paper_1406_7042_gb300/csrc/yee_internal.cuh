@@ -82,6 +82,8 @@ void yee_tma_tile(int *tx, int *ty);
 int yee_split_vw(const fdtd_grid *g);
 int yee_split_lz(const fdtd_grid *g);
 fdtd_status launch_yee_march(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s);
+int choose_kchunk(const fdtd_grid *g, int ntiles, int ctas_per_sm);
+int yee_march_vw(const fdtd_grid *g);
 fdtd_status launch_yee_split(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s);
 fdtd_status run_yee_stream(fdtd_grid *g, int64_t nsteps, const void *u, void *y, cudaStream_t s);
 fdtd_status launch_yee_tma(fdtd_grid *g, const void *u_row, void *y_row, int kchunk, cudaStream_t s);

@@ -1,22 +1,24 @@
 // A2 (large grids): the Yee leap-frog of Eq. (matrix) fused into one pass over
-// memory per step, with no block barriers and no shared memory.
+// memory per step.
 //
-// Each thread owns VW consecutive x cells of one row of a 32 VW x 8 tile and
-// marches up a chunk of z planes.  At plane k it computes E^{n+1}(k) for its
-// cells and, from the same input buffer, the two E^{n+1} components its H
-// update needs from outside: Ex, Ez of the row above (j + 1, recomputed by
-// this thread) and Ey, Ez of the next x cell (the next lane's own value by a
-// shuffle; the last lane recomputes it).  It then updates H^{n+3/2} one plane
-// behind, at k - 1, from E^{n+1} at k - 1 and k, so every value a thread needs
-// is its own or its neighbour's in the warp.  A chunk's top plane is computed
-// once more by the chunk above; nothing else is recomputed.  The new state
-// goes to the other buffer (ping-pong), so neighbours always read the old one.
+// A CTA of 8 warps (one per row) owns 7 rows of a 32 VW-cell-wide tile and
+// marches up a chunk of z planes; thread (tx, ty) owns VW consecutive x cells
+// of row ty.  At plane k every warp computes E^{n+1}(k) for its cells (warp 7
+// for the first row of the next tile, which the last owned row's H needs) and
+// publishes Ex, Ez in shared memory; the first lanes of warp 7 also compute
+// Ey, Ez of the +x halo column.  The owned rows then update H^{n+3/2} one
+// plane behind, at k - 1, from E^{n+1} at k - 1 (own cells, the next lane's by
+// a shuffle, the row above and the halo column from shared memory) and at k
+// (own cells).  One barrier per plane; the shared slots alternate with the
+// plane parity.  A chunk's top plane is computed once more by the chunk above.
+// The new state goes to the other buffer (ping-pong), so neighbours always
+// read the old one.
 //
 // DRAM sees each field value read once and written once per step (the 48 B
-// per cell of the fused form, plus the material map); the recomputed halo
-// reads come from L1/L2.  Sources and probes are applied afterwards by two
-// small kernels: the step is linear, so a source's effect on this step's H is
-// -Db curlE(dE) on the four H edges around the source edge.
+// per cell of the fused form, plus the material map); the halo row's and
+// chunk tops' reads come mostly from L2.  Sources and probes are applied
+// afterwards by two small kernels: the step is linear, so a source's effect on
+// this step's H is -Db curlE(dE) on the four H edges around the source edge.
 #include <algorithm>
 #include <vector>
 
@@ -60,25 +62,37 @@ __device__ __forceinline__ T e_comp_at(const YeeArgs<T, ID> &a, const ID *__rest
   return ca * __ldg(a.Ein + c * nc + n) + cb * curl;
 }
 
-template <typename T, typename ID, bool HOMOG_H, int VW>
-__global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+// CTAs per SM the register budget is sized for (MTY rows of 32 threads;
+// measured on 384 x 384 x 64: 8 rows beat 16, whose barrier spans twice the warps).
+template <typename T, int VW, int MTY>
+constexpr int march_min_blocks() {
+  return MTY > 8 ? 1 : (sizeof(T) == 8 ? 3 - VW : (VW == 4 ? 2 : 3));
+}
+
+template <typename T, typename ID, bool HOMOG_H, int VW, int MTY>
+__global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+  constexpr int OWN = MTY - 1;  // rows a CTA owns; the last warp computes E of the next tile's first row
+  constexpr int W = LTX * VW;   // cells per tile row
+  __shared__ T sx[2][MTY][W], sz[2][MTY][W];  // Ex, Ez of E^{n+1} by row, planes k & 1
+  __shared__ T sh[2][2][OWN];                 // Ey, Ez of E^{n+1} on the +x halo column
   wait_prior_grid();
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = (blockIdx.x * LTX + tx) * VW, j = blockIdx.y * LTY + ty;
-  const int k0 = blockIdx.z * lz, k1 = min(a.nz, k0 + lz);
+  const bool halo = ty == OWN;  // warp-uniform
   const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
   const int64_t nc = a.nc, plane = (int64_t)nx * ny;
   auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
-  if (j >= ny) {  // warp-uniform
-    allow_next_grid();
-    return;
-  }
-  const bool live = i0 < nx;
+  // this CTA: chunk blockIdx.z of tile (blockIdx.x, blockIdx.y)
+  {
+  const int k0 = blockIdx.z * lz, k1 = min(nz, k0 + lz);
+  const int bx = blockIdx.x, by = blockIdx.y;
+  const int i0 = (bx * LTX + tx) * VW, j0 = by * OWN, j = j0 + ty;
+  const bool live = i0 < nx && j < ny;
+  const int jc = min(j, ny - 1);
   const T *Hx = a.Hin, *Hy = a.Hin + nc, *Hz = a.Hin + 2 * nc;
   const ID *M = a.mat;
   const ID none = (ID)~(ID)0;
-  const T ryd = ax(AX_RDD, nx + j), wyl = ax(AX_WLO, nx + j), wyh = ax(AX_WHI, nx + j);
-  const T rdy = ax(AX_RD, nx + j);
+  const T ryd = ax(AX_RDD, nx + jc), wyl = ax(AX_WLO, nx + jc), wyh = ax(AX_WHI, nx + jc);
+  const T rdy = ax(AX_RD, nx + jc);
   T rxd[VW], rdx[VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
@@ -86,19 +100,27 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a
     rdx[e] = live ? ax(AX_RD, i0 + e) : T(0);
   }
   const T da0 = __ldg(a.ctab + 2 * a.nmat), db0 = __ldg(a.ctab + 3 * a.nmat);
-  // carried from plane k - 1: old H (own), new E (own, +x and +y neighbours)
-  T hx_p[VW], hy_p[VW], hz_p[VW], ex_p[VW], ey_p[VW], ez_p[VW], exy_p[VW], ezy_p[VW];
-  T eyx_p = T(0), ezx_p = T(0);
+  // the halo warp's first lanes compute Ey, Ez of the +x halo column ih (the
+  // next tile's first column) for the owned rows, carrying its old Hx
+  const int ih = (bx + 1) * W, jh = j0 + tx;
+  const bool xl = halo && tx < OWN && ih < nx && jh < ny;
+  const int64_t nhrow = (int64_t)min(jh, ny - 1) * nx + min(ih, nx - 1);
+  const T rxdh = xl ? ax(AX_RDD, ih) : T(0), rydh = xl ? ax(AX_RDD, nx + jh) : T(0);
+  // carried from plane k - 1: old H and new E of the own cells (and the halo cell)
+  T hx_p[VW], hy_p[VW], hz_p[VW], ex_p[VW], ey_p[VW], ez_p[VW];
 #pragma unroll
-  for (int e = 0; e < VW; ++e) hx_p[e] = hy_p[e] = hz_p[e] = ex_p[e] = ey_p[e] = ez_p[e] = exy_p[e] = ezy_p[e] = T(0);
-  int64_t n = k0 * plane + (int64_t)j * nx + i0;
+  for (int e = 0; e < VW; ++e) hx_p[e] = hy_p[e] = hz_p[e] = ex_p[e] = ey_p[e] = ez_p[e] = T(0);
+  T hxh_p = T(0);
+  int64_t n = k0 * plane + (int64_t)jc * nx + i0;
   if (live && k0 > 0) {
     ldv<VW, false>(hx_p, Hx + n - plane);
     ldv<VW, false>(hy_p, Hy + n - plane);
   }
+  if (xl && k0 > 0) hxh_p = __ldg(Hx + k0 * plane + nhrow - plane);
   for (int k = k0; k <= k1; ++k, n += plane) {
-    const bool top = k == k1;          // plane of the chunk above: Ex, Ey for H(k-1) only
+    const bool top = k == k1;  // plane of the chunk above: E for H(k-1) only
     const bool inbox = k < nz;
+    const int b = k & 1;
     T hx[VW], hy[VW], hz[VW], hx_jm[VW], hz_jm[VW], ex[VW], ey[VW], ez[VW];
     ID mu[VW];
 #pragma unroll
@@ -120,6 +142,20 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a
         hy_l = __ldg(Hy + n - 1);
         hz_l = __ldg(Hz + n - 1);
       }
+    }
+    T hxh = T(0), hxh_jm = T(0), hyh = T(0), hyh_m = T(0), hzh = T(0), hzh_m = T(0), eyh_o = T(0), ezh_o = T(0);
+    ID muh = none;
+    const int64_t nhc = k * plane + nhrow;
+    if (xl && inbox) {
+      hxh = __ldg(Hx + nhc);
+      if (jh > 0) hxh_jm = __ldg(Hx + nhc - nx);
+      hyh = __ldg(Hy + nhc);
+      hyh_m = __ldg(Hy + nhc - 1);
+      hzh = __ldg(Hz + nhc);
+      hzh_m = __ldg(Hz + nhc - 1);
+      eyh_o = __ldg(a.Ein + nc + nhc);
+      ezh_o = __ldg(a.Ein + 2 * nc + nhc);
+      muh = __ldg(emat + nhc);
     }
     const T hy_s = __shfl_up_sync(0xffffffffu, hy[VW - 1], 1), hz_s = __shfl_up_sync(0xffffffffu, hz[VW - 1], 1);
     if (tx > 0) { hy_l = hy_s; hz_l = hz_s; }
@@ -156,32 +192,55 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a
         oy[e] = cay * ey[e] + cby * ((hx[e] - hx_p[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
         oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
       }
-      if (!top) {
+      if (!top && !halo) {
         stv<VW>(a.Eout + n, ox);
         stv<VW>(a.Eout + nc + n, oy);
         stv<VW>(a.Eout + 2 * nc + n, oz);
       }
     }
-    // neighbours' E^{n+1}(k) for H(k): +y row (recomputed), +x cell (next lane)
-    T exy[VW], ezy[VW];
-#pragma unroll
-    for (int e = 0; e < VW; ++e) exy[e] = ezy[e] = T(0);
-    T eyx = __shfl_down_sync(0xffffffffu, oy[0], 1), ezx = __shfl_down_sync(0xffffffffu, oz[0], 1);
-    if (!top) {
-      if (live && inbox) {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          exy[e] = e_comp_at(a, emat, 0, i0 + e, j + 1, k);
-          ezy[e] = e_comp_at(a, emat, 2, i0 + e, j + 1, k);
+    if (halo && tx < OWN) {
+      T eyh = T(0), ezh = T(0);
+      if (xl && inbox) {
+        T ca1, cb1, ca2, cb2;
+        if (muh != none) {
+          ca1 = ca2 = __ldg(a.ctab + muh);
+          cb1 = cb2 = __ldg(a.ctab + a.nmat + muh);
+        } else {
+          const int64_t c = nhc;
+          const T wzl = ax(AX_WLO, nx + ny + k), wzh = ax(AX_WHI, nx + ny + k);
+          const T wxlh = ax(AX_WLO, ih), wxhh = ax(AX_WHI, ih);
+          const T wylh = ax(AX_WLO, nx + jh), wyhh = ax(AX_WHI, nx + jh);
+          const ID m = M[c], m_i = M[c - 1], m_j = jh > 0 ? M[c - nx] : m, m_k = k > 0 ? M[c - plane] : m;
+          const ID m_ij = jh > 0 ? M[c - 1 - nx] : m, m_ik = k > 0 ? M[c - 1 - plane] : m;
+          e_coef(a, m_ik, m_k, m_i, m, wxlh, wxhh, wzl, wzh, ca1, cb1);
+          e_coef(a, m_ij, m_j, m_i, m, wxlh, wxhh, wylh, wyhh, ca2, cb2);
         }
+        if (k == 0) ca1 = cb1 = T(0);
+        if (jh == 0) ca2 = cb2 = T(0);
+        const T rzd = ax(AX_RDD, nx + ny + k);
+        eyh = ca1 * eyh_o + cb1 * ((hxh - hxh_p) * rzd - (hzh - hzh_m) * rxdh);
+        ezh = ca2 * ezh_o + cb2 * ((hyh - hyh_m) * rxdh - (hxh - hxh_jm) * rydh);
+        hxh_p = hxh;
       }
-      if (tx == LTX - 1) {
-        eyx = live && inbox ? e_comp_at(a, emat, 1, i0 + VW, j, k) : T(0);
-        ezx = live && inbox ? e_comp_at(a, emat, 2, i0 + VW, j, k) : T(0);
-      }
+      sh[b][0][tx] = eyh;
+      sh[b][1][tx] = ezh;
     }
-    // H^{n+3/2}(k - 1) from E^{n+1}(k - 1) and E^{n+1}(k)
-    if (k > k0 && live) {
+    // publish the y neighbours of the row below
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      sx[b][ty][tx * VW + e] = ox[e];
+      sz[b][ty][tx * VW + e] = oz[e];
+    }
+    // H^{n+3/2}(k - 1) from E^{n+1}(k - 1) (own, the next lane's, and the row
+    // above's and the halo column's shared at k - 1 & 1, complete since the last
+    // barrier) and E^{n+1}(k) (own)
+    const int bp = b ^ 1;
+    T eyx = __shfl_down_sync(0xffffffffu, ey_p[0], 1), ezx = __shfl_down_sync(0xffffffffu, ez_p[0], 1);
+    if (tx == LTX - 1 && !halo) {
+      eyx = sh[bp][0][ty];
+      ezx = sh[bp][1][ty];
+    }
+    if (k > k0 && !halo && live) {
       const int kh = k - 1;
       const int64_t nh = n - plane;
       const T rdz = ax(AX_RD, nx + ny + kh);
@@ -197,10 +256,11 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a
           if (j > 0) h_coef(a, M[c - nx], m, ax(AX_WLO, nx + j), ax(AX_WHI, nx + j), da[1], db[1]);
           if (kh > 0) h_coef(a, M[c - plane], m, ax(AX_WLO, nx + ny + kh), ax(AX_WHI, nx + ny + kh), da[2], db[2]);
         }
-        const T ey_ip = e == VW - 1 ? eyx_p : ey_p[e + 1], ez_ip = e == VW - 1 ? ezx_p : ez_p[e + 1];
-        const T hxv = da[0] * hx_p[e] - db[0] * ((ezy_p[e] - ez_p[e]) * rdy - (oy[e] - ey_p[e]) * rdz);
+        const T ey_ip = e == VW - 1 ? eyx : ey_p[e + 1], ez_ip = e == VW - 1 ? ezx : ez_p[e + 1];
+        const T exy = sx[bp][ty + 1][tx * VW + e], ezy = sz[bp][ty + 1][tx * VW + e];
+        const T hxv = da[0] * hx_p[e] - db[0] * ((ezy - ez_p[e]) * rdy - (oy[e] - ey_p[e]) * rdz);
         const T hyv = da[1] * hy_p[e] - db[1] * ((ox[e] - ex_p[e]) * rdz - (ez_ip - ez_p[e]) * rdx[e]);
-        const T hzv = da[2] * hz_p[e] - db[2] * ((ey_ip - ey_p[e]) * rdx[e] - (exy_p[e] - ex_p[e]) * rdy);
+        const T hzv = da[2] * hz_p[e] - db[2] * ((ey_ip - ey_p[e]) * rdx[e] - (exy - ex_p[e]) * rdy);
         nhx[e] = i == 0 ? T(0) : hxv;
         nhy[e] = j == 0 ? T(0) : hyv;
         nhz[e] = kh == 0 ? T(0) : hzv;
@@ -217,11 +277,11 @@ __global__ void __launch_bounds__(LTX *LTY, 2) yee_march_kernel(YeeArgs<T, ID> a
       ex_p[e] = ox[e];
       ey_p[e] = oy[e];
       ez_p[e] = oz[e];
-      exy_p[e] = exy[e];
-      ezy_p[e] = ezy[e];
     }
-    eyx_p = eyx;
-    ezx_p = ezx;
+    // plane k's shared values are complete, and plane k - 1's are no longer
+    // read, before the next plane overwrites that slot
+    __syncthreads();
+  }
   }
   allow_next_grid();
 }
@@ -331,16 +391,23 @@ static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   return FDTD_OK;
 }
 
-template <typename T, typename ID, bool HH, int VW>
+template <typename T, typename ID, bool HH, int VW, int MTY>
 static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
   FDTD_CHECK(ensure_emat<ID>(g, s));
   FDTD_CHECK(ensure_flat(g, s));
   YeeArgs<T, ID> a = split_args<T, ID>(g);
   a.u = static_cast<const T *>(u_row);
   a.y = static_cast<T *>(y_row);
-  const int lz = std::min(g->nz, g->tune_lz > 0 ? g->tune_lz : env_int("FDTDMOR_LZ", 16));
-  const dim3 grid((g->nx + LTX * VW - 1) / (LTX * VW), (g->ny + LTY - 1) / LTY, (g->nz + lz - 1) / lz);
-  FDTD_CHECK_CUDA(launch_dependent(yee_march_kernel<T, ID, HH, VW>, grid, dim3(LTX, LTY), s, a, g->emat.as<ID>(), lz));
+  static int per_sm = 0;
+  if (!per_sm) {
+    FDTD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_march_kernel<T, ID, HH, VW, MTY>, LTX * MTY, 0));
+    per_sm = std::max(1, per_sm);
+  }
+  const int ntx = (g->nx + LTX * VW - 1) / (LTX * VW), nty = (g->ny + MTY - 2) / (MTY - 1);
+  const char *lz_env = getenv("FDTDMOR_LZ");
+  const int lz = std::min(g->nz, lz_env ? env_int("FDTDMOR_LZ", 16) : choose_kchunk(g, ntx * nty, per_sm));
+  const dim3 grid(ntx, nty, (g->nz + lz - 1) / lz);
+  FDTD_CHECK_CUDA(launch_dependent(yee_march_kernel<T, ID, HH, VW, MTY>, grid, dim3(LTX, MTY), s, a, g->emat.as<ID>(), lz));
   FDTD_CHECK(after_launch("yee_march_kernel"));
   if (g->nflat_src) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_src_kernel<T, ID, HH>, dim3((g->nflat_src + 127) / 128), dim3(128), s, a,
@@ -355,10 +422,24 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
   return FDTD_OK;
 }
 
+// Cells per thread: 16-byte rows (4 FP32 values) on grids wide enough to fill
+// the 128-cell tiles, else the split form's width.
+int yee_march_vw(const fdtd_grid *g) {
+  if (const char *e = getenv("FDTDMOR_MARCH_VW")) {
+    const int v = atoi(e);
+    if ((v == 1 || v == 2 || (v == 4 && g->elem == 4)) && g->nx % v == 0) return v;
+  }
+  if (g->elem == 4 && g->nx % 4 == 0 && g->nx >= 256) return 4;
+  return yee_split_vw(g);
+}
+
 template <typename T, typename ID, bool HH>
 static fdtd_status launch_march_t(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
-  if (yee_split_vw(g) == 2) return launch_march_v<T, ID, HH, 2>(g, u_row, y_row, s);
-  return launch_march_v<T, ID, HH, 1>(g, u_row, y_row, s);
+  const int vw = yee_march_vw(g);
+  if constexpr (sizeof(T) == 4)
+    if (vw == 4) return launch_march_v<T, ID, HH, 4, 8>(g, u_row, y_row, s);
+  if (vw == 2) return launch_march_v<T, ID, HH, 2, 8>(g, u_row, y_row, s);
+  return launch_march_v<T, ID, HH, 1, 8>(g, u_row, y_row, s);
 }
 
 fdtd_status launch_yee_march(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
