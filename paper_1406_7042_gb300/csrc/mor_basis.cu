@@ -1141,19 +1141,30 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
                                                  (int)hsm));
           block_axpy_kernel<T><<<ablk, 256, hsm, s>>>(n3, V, n3, qc, Hd.as<double>(), nbk, W, n_pad);
           FDTD_CHECK(after_launch("block_axpy_kernel"));
-          // second pass in FP32 with FP64 dot sums restores orthogonality to
-          // the field precision (the cancellation of nearly dependent Krylov
-          // vectors magnifies the first pass's TF32 / BF16 coefficient error)
-          for (int c = 0; c < nbk; ++c) {
-            double a0, a1;
-            FDTD_CHECK(bb.cgs2(w, V, n3, qc, W + (size_t)c * n_pad, n3, a0, a1, 1));
-          }
         }
         const int qb0 = qc;
         for (int c = 0; c < nbk; ++c) {
           T *wc = W + (size_t)c * n_pad;
+          // FP32 passes with FP64 dot sums against the columns before the
+          // block restore orthogonality to the field precision (the
+          // cancellation of nearly dependent Krylov vectors magnifies the
+          // first pass's TF32 / BF16 coefficient error); a pass that cancels
+          // more than half the norm is repeated (the "twice is enough" test)
+          for (int rep = 0; rep < 3 && qb0 > 0; ++rep) {
+            double a0, a1;
+            FDTD_CHECK(bb.cgs2(w, V, n3, qb0, wc, n3, a0, a1, 1));
+            if (a1 >= 0.5 * a0) break;
+          }
           double m0, n1;
           FDTD_CHECK(bb.cgs2(w, V + (size_t)qb0 * n3, n3, qc - qb0, wc, n3, m0, n1));
+          // a strong cancellation against the block's own columns re-exposes
+          // their small error along the earlier columns: one more FP32 pass
+          // against all columns
+          for (int rep = 0; rep < 2 && n1 < 0.5 * m0 && qc > 0; ++rep) {
+            double a0;
+            FDTD_CHECK(bb.cgs2(w, V, n3, qc, wc, n3, a0, n1, 1));
+            m0 = a0;
+          }
           if (n0[c] > 0 && n1 >= o.defl_tol * n0[c]) {
             scale_copy_kernel<T, T><<<std::min<int64_t>((n3 + 255) / 256, 152 * 16), 256, 0, s>>>(
                 n3, wc, V + (size_t)qc * n3, (T)(1.0 / n1));

@@ -348,3 +348,24 @@ def test_full_size_bench_workload_properties():
                       np.zeros((Dm.shape[0], m.get("BE").shape[1])), m.get("CE"))
     lam = np.abs(np.linalg.eigvals(mor.reduced_amplification(red, dt)))
     assert lam.max() <= 1.0 + 1e-6
+
+
+@pytest.mark.parametrize("orth", ["tf32", "bf16"])
+def test_tensor_core_gram_schmidt_many_blocks(orth):
+    """The 100x50x24 microstrip with order 100 (seven blocks of 16 pool
+    vectors, nearly dependent H parts): both halves of the tensor-core CGS2
+    basis orthonormal to FP32 level, and D~eps, D~mu positive definite (the
+    perturbation factorises them)."""
+    wl = W.config4(downscale=True)
+    grid = F.Grid(wl.grid, "f32")
+    dt0 = wl.s_ref * grid.cfl_dt()
+    b = F.Basis(grid, 100, dt0, wl.L, wl.M, wl.fmax, tol=1e-5, defl_tol=1e-5, orth=orth, allow_noconv=True)
+    for which in (1, 2):
+        V = b.V(which).double()
+        eye = torch.eye(V.shape[0], dtype=torch.float64, device="cuda")
+        assert float((V @ V.T - eye).abs().max()) <= 1e-4, which
+    m = F.Model(grid, b)
+    m.perturb(dt0)
+    for name in ("De", "Dm"):
+        D = m.get(name)
+        assert np.linalg.eigvalsh(0.5 * (D + D.T)).min() > 0, name
