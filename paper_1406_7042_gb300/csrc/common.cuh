@@ -141,6 +141,9 @@ struct fdtd_grid {
   bool flat_ready = false;
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
+  fdtdmor::DevBuf ecoef;        // per E edge (Ca x3, Cb x3 by cell) for small grids
+  int64_t ecoef_version = -1;   // ctab_version it was built from
+  int64_t ctab_version = 0;     // bumped by every rebuild of ctab
   fdtdmor::DevBuf uflag;        // per (tile, plane) uniform material id or -1 (fast Yee kernel)
   bool uflag_ready = false;
   fdtdmor::DevBuf errflag;      // set by kernels whose bounded device waits gave up

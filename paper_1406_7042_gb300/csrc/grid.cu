@@ -68,6 +68,7 @@ fdtd_status ensure_coef_table(fdtd_grid *g, double dt, cudaStream_t s) {
                                                g->ctab.as<float>());
   FDTD_CHECK(after_launch("coef_table_kernel"));
   g->ctab_dt = dt;
+  ++g->ctab_version;
   return FDTD_OK;
 }
 
@@ -352,6 +353,7 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->errflag.release(s);
   g->uflag.release(s);
   g->emat.release(s);
+  g->ecoef.release(s);
   g->gsync.release(s);
   g->u_graph.release(s);
   g->flat_src.release(s);

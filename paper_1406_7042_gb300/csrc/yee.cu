@@ -293,10 +293,10 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
                       (uint64_t)(uintptr_t)g->ctab.ptr,
                       (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
                       (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr,
-                      (uint64_t)(uintptr_t)g->emat.ptr,
+                      (uint64_t)(uintptr_t)g->emat.ptr ^ ((uint64_t)(uintptr_t)g->ecoef.ptr << 1),
                       (uint64_t)(uintptr_t)g->u_graph.ptr ^ ((uint64_t)(uintptr_t)g->y_graph.ptr << 1),
                       (uint64_t)g->lists.tx << 32 | (uint64_t)g->lists.ty,
-                      (uint64_t)(split ? yee_split_vw(g) + 8 * yee_march_vw(g) : 0) << 32 | (uint64_t)(split ? yee_split_lz(g) : 0) |
+                      (uint64_t)(split ? yee_split_vw(g) + 8 * yee_march_vw(g) + 64 * (int)yee_split_precoef(g) : 0) << 32 | (uint64_t)(split ? yee_split_lz(g) : 0) |
                           (uint64_t)(getenv("FDTDMOR_SLAB") ? atoi(getenv("FDTDMOR_SLAB")) : g->tune_slab) << 16,
                       (uint64_t)(uintptr_t)g->fields[0].ptr ^ ((uint64_t)(uintptr_t)g->fields[1].ptr << 1)};
   const int c = g->cur;

@@ -18,6 +18,7 @@ struct YeeArgs {
   const T *__restrict__ ax;    // axis tables (AX_COUNT x (nx+ny+nz))
   const T *__restrict__ mtab;  // eps, sig, mu, sigm, pec (5 x nmat)
   const T *__restrict__ ctab;  // ca, cb, da, db (4 x nmat)
+  const T *__restrict__ ecoef; // per-edge Ca (3 x nc) then Cb (3 x nc), or null
   int nmat;
   T inv_dt;
   const int32_t *__restrict__ src_ptr;
@@ -84,6 +85,7 @@ int yee_split_lz(const fdtd_grid *g);
 fdtd_status launch_yee_march(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s);
 int choose_kchunk(const fdtd_grid *g, int ntiles, int ctas_per_sm);
 int yee_march_vw(const fdtd_grid *g);
+bool yee_split_precoef(const fdtd_grid *g);
 fdtd_status launch_yee_split(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s);
 fdtd_status run_yee_stream(fdtd_grid *g, int64_t nsteps, const void *u, void *y, cudaStream_t s);
 fdtd_status launch_yee_tma(fdtd_grid *g, const void *u_row, void *y_row, int kchunk, cudaStream_t s);

@@ -25,12 +25,12 @@
 
 namespace fdtdmor {
 
-template <typename T, typename ID, int VW>
+template <typename T, typename ID, int VW, bool PRE>
 __global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 3 : 4) yee_e_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
                                                                         int kbase, int kend) {
   wait_prior_grid();
   const int k0 = kbase + blockIdx.z * lz;
-  e_unit<T, ID, false, VW>(a, emat, blockIdx.x, blockIdx.y, k0, min(kend, k0 + lz));
+  e_unit<T, ID, false, VW, PRE>(a, emat, blockIdx.x, blockIdx.y, k0, min(kend, k0 + lz));
   allow_next_grid();
 }
 
@@ -157,6 +157,14 @@ int yee_split_lz(const fdtd_grid *g) {
 }
 
 
+// Per-edge coefficient map for the E launches: on grids whose two field
+// buffers and the map (18 values per cell) fit in 64 MB of L2, where the
+// material averaging at interfaces, not memory, sets the E launch's time.
+bool yee_split_precoef(const fdtd_grid *g) {
+  if (const char *e = getenv("FDTDMOR_PRECOEF")) return atoi(e) != 0;
+  return (double)g->nc * g->elem * 18.0 <= 64.0 * (1 << 20);
+}
+
 // One step as an E launch and an H launch, out of place (fields[cur] ->
 // fields[cur ^ 1]).
 template <typename T, typename ID, bool HH, int VW>
@@ -165,6 +173,12 @@ static fdtd_status launch_split_v(fdtd_grid *g, const void *u_row, void *y_row, 
   YeeArgs<T, ID> a = split_args<T, ID>(g);
   a.u = static_cast<const T *>(u_row);
   a.y = static_cast<T *>(y_row);
+  const bool pre = yee_split_precoef(g);
+  if (pre) {
+    const fdtd_status st = ensure_ecoef<T, ID>(g, a, s);
+    FDTD_CHECK(st);
+    a.ecoef = g->ecoef.as<T>();
+  }
   const int lz = yee_split_lz(g);
   // z slabs ordered E(0), E(1), H(0), E(2), H(1), ...: H of slab s reads the
   // E^{n+1} and H^{n+1/2} of its slab soon after E(s) and E(s + 1) touched
@@ -177,7 +191,8 @@ static fdtd_status launch_split_v(fdtd_grid *g, const void *u_row, void *y_row, 
   auto E = [&](int q) -> fdtd_status {
     const int kb = q * slab, ke = std::min(g->nz, kb + slab);
     const dim3 grid(g->lists.ntx, g->lists.nty, (ke - kb + lz - 1) / lz);
-    FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW>, grid, block, s, a, emat, lz, kb, ke));
+    if (pre) FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW, true>, grid, block, s, a, emat, lz, kb, ke));
+    else FDTD_CHECK_CUDA(launch_dependent(yee_e_kernel<T, ID, VW, false>, grid, block, s, a, emat, lz, kb, ke));
     return after_launch("yee_e_kernel");
   };
   auto H = [&](int q) -> fdtd_status {

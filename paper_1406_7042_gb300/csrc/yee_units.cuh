@@ -92,6 +92,53 @@ __device__ __forceinline__ void ldids(ID (&r)[VW], const ID *p) {
   }
 }
 
+// (Ca, Cb) of the three E edges of cell c = (i, j, k): from the material
+// table where the cell's uniform-neighbourhood id mu is set, else the area
+// weighted edge average; zero on the walls (tangential E of the PEC box).
+template <typename T, typename ID>
+__device__ __forceinline__ void cell_e_coefs(const YeeArgs<T, ID> &a, ID mu, int64_t c, int i, int j, int k, T wyl,
+                                             T wyh, T (&ca)[3], T (&cb)[3]) {
+  const int nx = a.nx, ny = a.ny, ntot = nx + ny + a.nz;
+  const int64_t plane = (int64_t)nx * ny;
+  const ID none = (ID)~(ID)0;
+  if (mu != none) {
+    ca[0] = ca[1] = ca[2] = __ldg(a.ctab + mu);
+    cb[0] = cb[1] = cb[2] = __ldg(a.ctab + a.nmat + mu);
+  } else {
+    const ID *M = a.mat;
+    const T wxl = __ldg(a.ax + AX_WLO * ntot + i), wxh = __ldg(a.ax + AX_WHI * ntot + i);
+    const T wzl = __ldg(a.ax + AX_WLO * ntot + nx + ny + k), wzh = __ldg(a.ax + AX_WHI * ntot + nx + ny + k);
+    const ID m = M[c];
+    const ID m_i = i > 0 ? M[c - 1] : m, m_j = j > 0 ? M[c - nx] : m, m_k = k > 0 ? M[c - plane] : m;
+    const ID m_ij = (i > 0 && j > 0) ? M[c - 1 - nx] : m, m_ik = (i > 0 && k > 0) ? M[c - 1 - plane] : m;
+    const ID m_jk = (j > 0 && k > 0) ? M[c - nx - plane] : m;
+    e_coef(a, m_jk, m_k, m_j, m, wyl, wyh, wzl, wzh, ca[0], cb[0]);
+    e_coef(a, m_ik, m_k, m_i, m, wxl, wxh, wzl, wzh, ca[1], cb[1]);
+    e_coef(a, m_ij, m_j, m_i, m, wxl, wxh, wyl, wyh, ca[2], cb[2]);
+  }
+  if (j == 0 || k == 0) ca[0] = cb[0] = T(0);
+  if (i == 0 || k == 0) ca[1] = cb[1] = T(0);
+  if (i == 0 || j == 0) ca[2] = cb[2] = T(0);
+}
+
+// The per-edge coefficient map of a grid: what e_unit computes per cell,
+// stored once (Ca of x, y, z edges, then Cb of x, y, z, each nc long).
+template <typename T, typename ID>
+__global__ void ecoef_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, T *__restrict__ out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  if (n >= a.nc) return;
+  const int i = (int)(n % a.nx), j = (int)((n / a.nx) % a.ny), k = (int)(n / plane);
+  const int ntot = a.nx + a.ny + a.nz;
+  const T wyl = __ldg(a.ax + AX_WLO * ntot + a.nx + j), wyh = __ldg(a.ax + AX_WHI * ntot + a.nx + j);
+  T ca[3], cb[3];
+  cell_e_coefs(a, emat[n], n, i, j, k, wyl, wyh, ca, cb);
+  for (int c = 0; c < 3; ++c) {
+    out[c * a.nc + n] = ca[c];
+    out[(3 + c) * a.nc + n] = cb[c];
+  }
+}
+
 // E^{n+1} on planes [k0, k1) of tile (bx, by), which spans LTX * VW cells in
 // x: thread (tx, ty) owns cells i0 .. i0 + VW - 1 of row j and marches in z.
 // The x neighbour i0 - 1 comes from the lane to the left (a shuffle) or, for
@@ -99,7 +146,11 @@ __device__ __forceinline__ void ldids(ID (&r)[VW], const ID *p) {
 // past the end of a row (whose loads read as zero) still feed the shuffles.
 // In place when a.Eout == a.Ein: the only E value read is the one written by
 // the same thread, and the store depends on it.
-template <typename T, typename ID, bool COH, int VW>
+//
+// With PRE the coefficients come from the per-edge map a.ecoef (six more
+// vector loads, no material lookups): the form for small, L2-resident grids,
+// where the averaging at material interfaces would set the pace.
+template <typename T, typename ID, bool COH, int VW, bool PRE = false>
 __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__restrict__ emat, int bx, int by,
                                        int k0, int k1) {
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * LTX + tx;
@@ -114,8 +165,6 @@ __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__rest
 #pragma unroll
     for (int e = 0; e < VW; ++e) rxd[e] = live ? ax(AX_RDD, i0 + e) : T(0);
     const T *Hx = a.Hin, *Hy = a.Hin + nc, *Hz = a.Hin + 2 * nc;
-    const ID *M = a.mat;
-    const ID none = (ID)~(ID)0;
     int64_t n = k0 * plane + (int64_t)j * nx + i0;
     T hx_km[VW], hy_km[VW];
 #pragma unroll
@@ -127,10 +176,18 @@ __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__rest
     for (int k = k0; k < k1; ++k, n += plane) {
       T hx[VW], hy[VW], hz[VW], hx_jm[VW], hz_jm[VW], ex[VW], ey[VW], ez[VW];
       ID mu[VW];
+      T pca[3][VW], pcb[3][VW];  // per-edge coefficients (PRE)
 #pragma unroll
       for (int e = 0; e < VW; ++e) hx[e] = hy[e] = hz[e] = hx_jm[e] = hz_jm[e] = ex[e] = ey[e] = ez[e] = T(0);
       T hy_l = T(0), hz_l = T(0);  // Hy, Hz at i0 - 1 for lane 0
       if (live) {
+        if constexpr (PRE) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            ldv<VW, COH>(pca[c], a.ecoef + c * nc + n);
+            ldv<VW, COH>(pcb[c], a.ecoef + (3 + c) * nc + n);
+          }
+        }
         ldv<VW, COH>(hx, Hx + n);
         ldv<VW, COH>(hy, Hy + n);
         ldv<VW, COH>(hz, Hz + n);
@@ -141,7 +198,7 @@ __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__rest
         ldv<VW, COH>(ex, a.Ein + n);
         ldv<VW, COH>(ey, a.Ein + nc + n);
         ldv<VW, COH>(ez, a.Ein + 2 * nc + n);
-        ldids<VW>(mu, emat + n);
+        if constexpr (!PRE) ldids<VW>(mu, emat + n);
         if (tx == 0 && i0 > 0) {
           hy_l = ldf<COH>(Hy + n - 1);
           hz_l = ldf<COH>(Hz + n - 1);
@@ -157,24 +214,15 @@ __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__rest
           const int i = i0 + e;
           const T hy_im = e == 0 ? hy_l : hy[e - 1], hz_im = e == 0 ? hz_l : hz[e - 1];
           T cax, cbx, cay, cby, caz, cbz;
-          if (mu[e] != none) {
-            cax = cay = caz = __ldg(a.ctab + mu[e]);
-            cbx = cby = cbz = __ldg(a.ctab + a.nmat + mu[e]);
+          if constexpr (PRE) {
+            cax = pca[0][e]; cay = pca[1][e]; caz = pca[2][e];
+            cbx = pcb[0][e]; cby = pcb[1][e]; cbz = pcb[2][e];
           } else {
-            const int64_t c = n + e;
-            const T wxl = ax(AX_WLO, i), wxh = ax(AX_WHI, i);
-            const T wzl = ax(AX_WLO, nx + ny + k), wzh = ax(AX_WHI, nx + ny + k);
-            const ID m = M[c];
-            const ID m_i = i > 0 ? M[c - 1] : m, m_j = j > 0 ? M[c - nx] : m, m_k = k > 0 ? M[c - plane] : m;
-            const ID m_ij = (i > 0 && j > 0) ? M[c - 1 - nx] : m, m_ik = (i > 0 && k > 0) ? M[c - 1 - plane] : m;
-            const ID m_jk = (j > 0 && k > 0) ? M[c - nx - plane] : m;
-            e_coef(a, m_jk, m_k, m_j, m, wyl, wyh, wzl, wzh, cax, cbx);
-            e_coef(a, m_ik, m_k, m_i, m, wxl, wxh, wzl, wzh, cay, cby);
-            e_coef(a, m_ij, m_j, m_i, m, wxl, wxh, wyl, wyh, caz, cbz);
+            T ca[3], cb[3];
+            cell_e_coefs(a, mu[e], n + e, i, j, k, wyl, wyh, ca, cb);
+            cax = ca[0]; cay = ca[1]; caz = ca[2];
+            cbx = cb[0]; cby = cb[1]; cbz = cb[2];
           }
-          if (j == 0 || k == 0) cax = cbx = T(0);
-          if (i == 0 || k == 0) cay = cby = T(0);
-          if (i == 0 || j == 0) caz = cbz = T(0);
           ox[e] = cax * ex[e] + cbx * ((hz[e] - hz_jm[e]) * ryd - (hy[e] - hy_km[e]) * rzd);
           oy[e] = cay * ey[e] + cby * ((hx[e] - hx_km[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
           oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
@@ -355,6 +403,7 @@ inline YeeArgs<T, ID> split_args(fdtd_grid *g) {
   a.ax = g->axis.as<T>();
   a.mtab = g->mtab.as<T>();
   a.ctab = g->ctab.as<T>();
+  a.ecoef = nullptr;
   a.nmat = g->nmat;
   a.inv_dt = (T)(1.0 / g->ctab_dt);
   a.src_ptr = g->lists.src_ptr.as<int32_t>();
@@ -373,6 +422,18 @@ inline fdtd_status ensure_emat(fdtd_grid *g, cudaStream_t s) {
   emat_kernel<ID><<<(int)((g->nc + 255) / 256), 256, 0, s>>>(g->mat.as<ID>(), g->nx, g->ny, g->nz, g->emat.as<ID>());
   FDTD_CHECK(after_launch("emat_kernel"));
   g->emat_ready = true;
+  return FDTD_OK;
+}
+
+// The per-edge coefficient map for the current coefficient table.
+template <typename T, typename ID>
+inline fdtd_status ensure_ecoef(fdtd_grid *g, const YeeArgs<T, ID> &a, cudaStream_t s) {
+  if (g->ecoef_version == g->ctab_version && g->ecoef.ptr) return FDTD_OK;
+  FDTD_CHECK(ensure_emat<ID>(g, s));
+  FDTD_CHECK(g->ecoef.alloc((size_t)6 * g->nc * sizeof(T), s));
+  ecoef_kernel<T, ID><<<(int)((g->nc + 255) / 256), 256, 0, s>>>(a, g->emat.as<ID>(), g->ecoef.as<T>());
+  FDTD_CHECK(after_launch("ecoef_kernel"));
+  g->ecoef_version = g->ctab_version;
   return FDTD_OK;
 }
 

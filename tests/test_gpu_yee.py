@@ -245,3 +245,33 @@ def test_absorbing_microstrip_parity(prec, tol):
         assert _rel(yg, yo) <= tol
         for c in range(6):
             assert _rel(fg[c], fo[c]) <= 10 * tol, c
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_edge_coefficient_map_is_bit_exact(monkeypatch, prec):
+    """The split form's E launch with the per-edge coefficient map (the small
+    grid default) and with the per-cell material lookups give the same fields,
+    also after the materials change (the map follows the table): bit-exact in
+    FP64; in FP32 the compiler may contract the coefficient arithmetic
+    differently in the two contexts, so within a few FP32 roundings."""
+    grid = ragged_grid(nx=26, ny=15, nz=12, seed=71)
+    dt = 0.95 * yee.cfl_dt(grid)
+    u = drive(grid, dt, 90)
+    out = {}
+    for pre in ("0", "1"):
+        monkeypatch.setenv("FDTDMOR_PRECOEF", pre)
+        g = F.Grid(grid, prec)
+        g.set_kernel("split")
+        ut = torch.tensor(u, dtype=g.dtype, device="cuda")
+        y1 = g.step(dt, ut, reset=True)
+        eps = grid.eps_r.copy()
+        eps[1:] *= 1.3
+        g.set_materials(eps)
+        y2 = g.step(dt, ut, reset=True)
+        out[pre] = (y1.cpu().numpy(), y2.cpu().numpy(), g.fields().cpu().numpy())
+    for a, b in zip(out["0"], out["1"]):
+        if prec == "f64":
+            assert np.array_equal(a, b)
+        else:
+            assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
+    assert np.max(np.abs(out["1"][0] - out["1"][1])) > 1e-3 * np.abs(out["1"][0]).max()
