@@ -51,7 +51,7 @@ __device__ __forceinline__ YeeArgs<T, ID> batch_args(const BatchGrid<T, ID> &bg,
   return a;
 }
 
-template <typename T, typename ID, int VW>
+template <typename T, typename ID, int VW, bool PRE>
 __global__ void __launch_bounds__(LTX *LTY, 3) yee_batch_e_kernel(const BatchGrid<T, ID> *__restrict__ grids,
                                                                  const BatchUnit *__restrict__ units, int nunits,
                                                                  const long long *__restrict__ step) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(LTX *LTY, 3) yee_batch_e_kernel(const BatchGri
     const BatchUnit un = units[w];
     const BatchGrid<T, ID> &bg = grids[un.grid];
     const YeeArgs<T, ID> a = batch_args(bg, n);
-    e_unit<T, ID, false, VW>(a, bg.emat, un.bx, un.by, un.k0, un.k1);
+    e_unit<T, ID, false, VW, PRE>(a, bg.emat, un.bx, un.by, un.k0, un.k1);
   }
   allow_next_grid();
 }
@@ -98,7 +98,7 @@ struct BatchGroup {
   virtual void release(cudaStream_t s) = 0;
 };
 
-template <typename T, typename ID, bool HH, int VW>
+template <typename T, typename ID, bool HH, int VW, bool PRE>
 struct BatchGroupT : BatchGroup {
   DevBuf grids, units;
   int nunits = 0;
@@ -111,6 +111,11 @@ struct BatchGroupT : BatchGroup {
       FDTD_CHECK(ensure_emat<ID>(g, s));
       BatchGrid<T, ID> &b = hg[q];
       b.a = split_args<T, ID>(g);
+      if (PRE) {
+        const fdtd_status st = ensure_ecoef<T, ID>(g, b.a, s);
+        FDTD_CHECK(st);
+        b.a.ecoef = g->ecoef.as<T>();
+      }
       b.f[0] = g->fields[0].as<T>();
       b.f[1] = g->fields[1].as<T>();
       b.c0 = g->cur;
@@ -138,7 +143,7 @@ struct BatchGroupT : BatchGroup {
   int blocks() const { return std::max(1, std::min(nunits, 16 * device_sms())); }
   fdtd_status launch_e(cudaStream_t s, const long long *step) override {
     if (!nunits) return FDTD_OK;
-    FDTD_CHECK_CUDA(launch_dependent(yee_batch_e_kernel<T, ID, VW>, dim3(blocks()), dim3(LTX, LTY), s,
+    FDTD_CHECK_CUDA(launch_dependent(yee_batch_e_kernel<T, ID, VW, PRE>, dim3(blocks()), dim3(LTX, LTY), s,
                                      grids.as<const BatchGrid<T, ID>>(), units.as<const BatchUnit>(), nunits, step));
     return after_launch("yee_batch_e_kernel");
   }
@@ -154,22 +159,29 @@ struct BatchGroupT : BatchGroup {
   }
 };
 
-template <typename T, typename ID, bool HH>
+template <typename T, typename ID, bool HH, bool PRE>
 static BatchGroup *make_group_vw(int vw) {
   if constexpr (sizeof(T) == 4) {
-    if (vw == 4) return new BatchGroupT<T, ID, HH, 4>();
+    if (vw == 4) return new BatchGroupT<T, ID, HH, 4, PRE>();
   }
-  if (vw == 2) return new BatchGroupT<T, ID, HH, 2>();
-  return new BatchGroupT<T, ID, HH, 1>();
+  if (vw == 2) return new BatchGroupT<T, ID, HH, 2, PRE>();
+  return new BatchGroupT<T, ID, HH, 1, PRE>();
 }
 
-static BatchGroup *make_group(fdtd_prec prec, int id_bytes, bool hh, int vw) {
+template <typename T, typename ID, bool HH>
+static BatchGroup *make_group_pre(int vw, bool pre) {
+  return pre ? make_group_vw<T, ID, HH, true>(vw) : make_group_vw<T, ID, HH, false>(vw);
+}
+
+static BatchGroup *make_group(fdtd_prec prec, int id_bytes, bool hh, int vw, bool pre) {
   if (prec == FDTD_F64) {
-    if (id_bytes == 1) return hh ? make_group_vw<double, uint8_t, true>(vw) : make_group_vw<double, uint8_t, false>(vw);
-    return hh ? make_group_vw<double, uint16_t, true>(vw) : make_group_vw<double, uint16_t, false>(vw);
+    if (id_bytes == 1)
+      return hh ? make_group_pre<double, uint8_t, true>(vw, pre) : make_group_pre<double, uint8_t, false>(vw, pre);
+    return hh ? make_group_pre<double, uint16_t, true>(vw, pre) : make_group_pre<double, uint16_t, false>(vw, pre);
   }
-  if (id_bytes == 1) return hh ? make_group_vw<float, uint8_t, true>(vw) : make_group_vw<float, uint8_t, false>(vw);
-  return hh ? make_group_vw<float, uint16_t, true>(vw) : make_group_vw<float, uint16_t, false>(vw);
+  if (id_bytes == 1)
+    return hh ? make_group_pre<float, uint8_t, true>(vw, pre) : make_group_pre<float, uint8_t, false>(vw, pre);
+  return hh ? make_group_pre<float, uint16_t, true>(vw, pre) : make_group_pre<float, uint16_t, false>(vw, pre);
 }
 
 // Leap-frog steps per captured graph.
@@ -187,7 +199,7 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
     FDTD_REQUIRE(nsteps == 0 || g->probes.empty() || (y && y[q]), "fdtd_step_batched: y[%d] is required", q);
   }
   if (nsteps == 0) return FDTD_OK;
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
   for (int q = 0; q < ngrids; ++q) {
     fdtd_grid *g = grids[q];
     FDTD_CHECK(ensure_coef_table(g, dt[q], s));
@@ -196,7 +208,7 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
     if (reset_fields) FDTD_CHECK_CUDA(cudaMemsetAsync(g->fields[g->cur].ptr, 0, (size_t)6 * g->nc * g->elem, s));
     const int p = (int)g->probes.size();
     if (p) FDTD_CHECK_CUDA(cudaMemsetAsync(y[q], 0, (size_t)nsteps * p * g->elem, s));
-    groups[std::make_tuple((int)g->prec, g->id_bytes, (int)g->homog_h, vw)].push_back(q);
+    groups[std::make_tuple((int)g->prec, g->id_bytes, (int)g->homog_h, vw, (int)yee_split_precoef(g))].push_back(q);
   }
   std::vector<BatchGroup *> gl;
   DevBuf step;
@@ -217,7 +229,7 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
   } cleanup{gl, step, cap, exec, s};
   for (auto &kv : groups) {
     const int prec = std::get<0>(kv.first), idb = std::get<1>(kv.first), hh = std::get<2>(kv.first),
-              vw = std::get<3>(kv.first);
+              vw = std::get<3>(kv.first), pre = std::get<4>(kv.first);
     std::vector<fdtd_grid *> gs;
     std::vector<const void *> us;
     std::vector<void *> ys;
@@ -226,7 +238,7 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
       us.push_back(grids[q]->ports.empty() ? nullptr : u[q]);
       ys.push_back(grids[q]->probes.empty() ? nullptr : y[q]);
     }
-    BatchGroup *b = make_group((fdtd_prec)prec, idb, hh != 0, vw);
+    BatchGroup *b = make_group((fdtd_prec)prec, idb, hh != 0, vw, pre != 0);
     gl.push_back(b);
     FDTD_CHECK(b->build(gs, us, ys, s));
   }
