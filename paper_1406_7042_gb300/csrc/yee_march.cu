@@ -20,8 +20,10 @@
 // afterwards by two small kernels: the step is linear, so a source's effect on
 // this step's H is -Db curlE(dE) on the four H edges around the source edge.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
+#include "tma_util.cuh"
 #include "yee_units.cuh"
 
 namespace fdtdmor {
@@ -62,6 +64,24 @@ __device__ __forceinline__ T e_comp_at(const YeeArgs<T, ID> &a, const ID *__rest
   return ca * __ldg(a.Ein + c * nc + n) + cb * curl;
 }
 
+// TMA staging of the 4-cell FP32 form: per plane, boxes of the tile with its
+// halos, x from i0 - 4 (H: the -x neighbour column and the +x halo column at
+// i0 + 128) or i0 (E, material map: the +x halo column), y from j0 - 1 (H: the
+// row below the tile) or j0, S planes in flight, one mbarrier per slot.
+struct MarchMaps {
+  CUtensorMap H[3], E[3], M;
+};
+template <typename ID>
+struct MarchStage {
+  static constexpr int HX = 136, HY = 9, EX = 132, EY = 8, MX = 144, MY = 8;
+  static constexpr int rup(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int HB = rup(HX * HY * 4), EB = rup(EX * EY * 4), MB = rup(MX * MY * (int)sizeof(ID));
+  static constexpr int BYTES = 3 * HB + 3 * EB + MB;
+  static constexpr uint32_t TX = 3u * HX * HY * 4 + 3u * EX * EY * 4 + MX * MY * sizeof(ID);
+  static constexpr int S = 3;
+  static constexpr size_t SMEM = (size_t)S * BYTES + S * sizeof(uint64_t);
+};
+
 // CTAs per SM the register budget is sized for (MTY rows of 32 threads;
 // measured on 384 x 384 x 64: 8 rows beat 16, whose barrier spans twice the warps).
 template <typename T, int VW, int MTY>
@@ -69,12 +89,23 @@ constexpr int march_min_blocks() {
   return MTY > 8 ? 1 : (sizeof(T) == 8 ? 3 - VW : (VW == 4 ? 2 : 3));
 }
 
-template <typename T, typename ID, bool HOMOG_H, int VW, int MTY>
-__global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz) {
+//
+// STAGED (FP32, 4 cells per thread, 8 warps): the plane inputs arrive in
+// shared memory by TMA, S planes ahead, instead of per-thread loads; waits are
+// bounded and a wait that gives up sets *err and ends the CTA after its copies
+// in flight have landed.
+template <typename T, typename ID, bool HOMOG_H, int VW, int MTY, bool STAGED>
+__global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
+                                                                                            const __grid_constant__ MarchMaps maps,
+                                                                                            unsigned *err) {
   constexpr int OWN = MTY - 1;  // rows a CTA owns; the last warp computes E of the next tile's first row
   constexpr int W = LTX * VW;   // cells per tile row
+  static_assert(!STAGED || (sizeof(T) == 4 && VW == 4 && MTY == 8), "staged form: FP32, 4 cells, 8 warps");
+  using St = MarchStage<ID>;
   __shared__ T sx[2][MTY][W], sz[2][MTY][W];  // Ex, Ez of E^{n+1} by row, planes k & 1
   __shared__ T sh[2][2][OWN];                 // Ey, Ez of E^{n+1} on the +x halo column
+  extern __shared__ __align__(128) unsigned char stg[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stg + (STAGED ? St::S * St::BYTES : 0));
   wait_prior_grid();
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool halo = ty == OWN;  // warp-uniform
@@ -117,45 +148,124 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
     ldv<VW, false>(hy_p, Hy + n - plane);
   }
   if (xl && k0 > 0) hxh_p = __ldg(Hx + k0 * plane + nhrow - plane);
+  // staged: planes k0 .. kmax are loaded, plane k0 + r into slot r % S
+  const int kmax = min(k1, nz - 1), nload = kmax - k0 + 1;
+  const int i0t = bx * W;
+  const int tid = ty * LTX + tx;
+  bool ok = true;
+  int waited = -1, issued = -1;
+  auto issue = [&](int r) {
+    unsigned char *st = stg + (r % St::S) * St::BYTES;
+    uint64_t *bar = &bars[r % St::S];
+    const int kk = k0 + r;
+    mbar_expect_tx(bar, St::TX);
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + c * St::HB, &maps.H[c], i0t - 4, j0 - 1, kk, bar);
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + 3 * St::HB + c * St::EB, &maps.E[c], i0t, j0, kk, bar);
+    tma_load_3d(st + 3 * St::HB + 3 * St::EB, &maps.M, i0t, j0, kk, bar);
+    issued = r;
+  };
+  if constexpr (STAGED) {
+    if (tid == 0) {
+      for (int q = 0; q < St::S; ++q) mbar_init(&bars[q], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (int r = 0; r < min(St::S, nload); ++r) issue(r);
+    }
+    __syncthreads();
+  }
   for (int k = k0; k <= k1; ++k, n += plane) {
     const bool top = k == k1;  // plane of the chunk above: E for H(k-1) only
     const bool inbox = k < nz;
     const int b = k & 1;
+    const int r = k - k0;
+    const unsigned char *st = stg + (r % St::S) * St::BYTES;
+    if constexpr (STAGED) {
+      if (k <= kmax) {
+        if (mbar_wait(&bars[r % St::S], (r / St::S) & 1)) waited = r;
+        else ok = false;
+      }
+    }
+    // staged reads: component c of H (rows j0 - 1 .. j0 + 7, x from i0t - 4),
+    // of E and of the material map (rows j0 .. j0 + 7, x from i0t)
+    auto hs = [&](int c, int row, int x) -> const float * {
+      return reinterpret_cast<const float *>(st + c * St::HB) + row * St::HX + x;
+    };
+    auto es = [&](int c, int row, int x) -> const float * {
+      return reinterpret_cast<const float *>(st + 3 * St::HB + c * St::EB) + row * St::EX + x;
+    };
+    auto ms = [&](int row, int x) -> const ID * {
+      return reinterpret_cast<const ID *>(st + 3 * St::HB + 3 * St::EB) + row * St::MX + x;
+    };
     T hx[VW], hy[VW], hz[VW], hx_jm[VW], hz_jm[VW], ex[VW], ey[VW], ez[VW];
     ID mu[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) hx[e] = hy[e] = hz[e] = hx_jm[e] = hz_jm[e] = ex[e] = ey[e] = ez[e] = T(0);
     T hy_l = T(0), hz_l = T(0);
     if (live && inbox) {
-      ldv<VW, false>(hx, Hx + n);
-      ldv<VW, false>(hy, Hy + n);
-      ldv<VW, false>(hz, Hz + n);
-      if (j > 0) {
-        ldv<VW, false>(hx_jm, Hx + n - nx);
-        ldv<VW, false>(hz_jm, Hz + n - nx);
-      }
-      ldv<VW, false>(ex, a.Ein + n);
-      ldv<VW, false>(ey, a.Ein + nc + n);
-      ldv<VW, false>(ez, a.Ein + 2 * nc + n);
-      ldids<VW>(mu, emat + n);
-      if (tx == 0 && i0 > 0) {
-        hy_l = __ldg(Hy + n - 1);
-        hz_l = __ldg(Hz + n - 1);
+      if constexpr (STAGED) {
+        const int xo = 4 + tx * VW;
+        auto ld4 = [](T (&r4)[VW], const float *p) {
+          const float4 v = *reinterpret_cast<const float4 *>(p);
+          r4[0] = v.x; r4[1] = v.y; r4[2] = v.z; r4[3] = v.w;
+        };
+        if constexpr (VW == 4) {
+          ld4(hx, hs(0, ty + 1, xo));
+          ld4(hy, hs(1, ty + 1, xo));
+          ld4(hz, hs(2, ty + 1, xo));
+          ld4(hx_jm, hs(0, ty, xo));   // zero-filled below the grid
+          ld4(hz_jm, hs(2, ty, xo));
+          ld4(ex, es(0, ty, tx * VW));
+          ld4(ey, es(1, ty, tx * VW));
+          ld4(ez, es(2, ty, tx * VW));
+          const ID *mp = ms(ty, tx * VW);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) mu[e] = mp[e];
+          hy_l = *hs(1, ty + 1, 3);    // x = i0 - 1 (zero-filled left of the grid)
+          hz_l = *hs(2, ty + 1, 3);
+        }
+      } else {
+        ldv<VW, false>(hx, Hx + n);
+        ldv<VW, false>(hy, Hy + n);
+        ldv<VW, false>(hz, Hz + n);
+        if (j > 0) {
+          ldv<VW, false>(hx_jm, Hx + n - nx);
+          ldv<VW, false>(hz_jm, Hz + n - nx);
+        }
+        ldv<VW, false>(ex, a.Ein + n);
+        ldv<VW, false>(ey, a.Ein + nc + n);
+        ldv<VW, false>(ez, a.Ein + 2 * nc + n);
+        ldids<VW>(mu, emat + n);
+        if (tx == 0 && i0 > 0) {
+          hy_l = __ldg(Hy + n - 1);
+          hz_l = __ldg(Hz + n - 1);
+        }
       }
     }
     T hxh = T(0), hxh_jm = T(0), hyh = T(0), hyh_m = T(0), hzh = T(0), hzh_m = T(0), eyh_o = T(0), ezh_o = T(0);
     ID muh = none;
     const int64_t nhc = k * plane + nhrow;
     if (xl && inbox) {
-      hxh = __ldg(Hx + nhc);
-      if (jh > 0) hxh_jm = __ldg(Hx + nhc - nx);
-      hyh = __ldg(Hy + nhc);
-      hyh_m = __ldg(Hy + nhc - 1);
-      hzh = __ldg(Hz + nhc);
-      hzh_m = __ldg(Hz + nhc - 1);
-      eyh_o = __ldg(a.Ein + nc + nhc);
-      ezh_o = __ldg(a.Ein + 2 * nc + nhc);
-      muh = __ldg(emat + nhc);
+      if constexpr (STAGED) {
+        // halo cell (i0t + 128, j0 + tx): staged x 132 (H) / 128 (E, map)
+        hxh = *hs(0, tx + 1, 4 + W);
+        hxh_jm = *hs(0, tx, 4 + W);
+        hyh = *hs(1, tx + 1, 4 + W);
+        hyh_m = *hs(1, tx + 1, 3 + W);
+        hzh = *hs(2, tx + 1, 4 + W);
+        hzh_m = *hs(2, tx + 1, 3 + W);
+        eyh_o = *es(1, tx, W);
+        ezh_o = *es(2, tx, W);
+        muh = *ms(tx, W);
+      } else {
+        hxh = __ldg(Hx + nhc);
+        if (jh > 0) hxh_jm = __ldg(Hx + nhc - nx);
+        hyh = __ldg(Hy + nhc);
+        hyh_m = __ldg(Hy + nhc - 1);
+        hzh = __ldg(Hz + nhc);
+        hzh_m = __ldg(Hz + nhc - 1);
+        eyh_o = __ldg(a.Ein + nc + nhc);
+        ezh_o = __ldg(a.Ein + 2 * nc + nhc);
+        muh = __ldg(emat + nhc);
+      }
     }
     const T hy_s = __shfl_up_sync(0xffffffffu, hy[VW - 1], 1), hz_s = __shfl_up_sync(0xffffffffu, hz[VW - 1], 1);
     if (tx > 0) { hy_l = hy_s; hz_l = hz_s; }
@@ -192,7 +302,7 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
         oy[e] = cay * ey[e] + cby * ((hx[e] - hx_p[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
         oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
       }
-      if (!top && !halo) {
+      if (!top && !halo && ok) {
         stv<VW>(a.Eout + n, ox);
         stv<VW>(a.Eout + nc + n, oy);
         stv<VW>(a.Eout + 2 * nc + n, oz);
@@ -240,7 +350,7 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
       eyx = sh[bp][0][ty];
       ezx = sh[bp][1][ty];
     }
-    if (k > k0 && !halo && live) {
+    if (k > k0 && !halo && live && ok) {
       const int kh = k - 1;
       const int64_t nh = n - plane;
       const T rdz = ax(AX_RD, nx + ny + kh);
@@ -280,7 +390,27 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
     }
     // plane k's shared values are complete, and plane k - 1's are no longer
     // read, before the next plane overwrites that slot
-    __syncthreads();
+    if constexpr (STAGED) {
+      if (__syncthreads_or(!ok)) break;
+      // every thread is done with slot r % S: refill it with plane r + S
+      if (tid == 0 && r + St::S < nload) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(r + St::S);
+      }
+    } else {
+      __syncthreads();
+    }
+  }
+  if constexpr (STAGED) {
+    if (!ok) {
+      // a wait gave up: record it, then let the copies in flight land
+      // (bounded) before the CTA's shared memory is released
+      if (tid == 0) {
+        atomicExch(err, 1u);
+        for (int rr = waited + 1; rr <= issued; ++rr) mbar_wait(&bars[rr % St::S], (rr / St::S) & 1);
+      }
+      __syncthreads();
+    }
   }
   }
   allow_next_grid();
@@ -391,6 +521,64 @@ static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   return FDTD_OK;
 }
 
+// Tensor maps of the staged form for both state buffers of the last grid used.
+struct MarchMapCache {
+  MarchMaps maps[2];
+  const void *f0 = nullptr, *f1 = nullptr, *emat = nullptr;
+  int64_t nc = 0;
+};
+
+// The staged form needs 16-byte rows of the fields and of the material map.
+static bool march_staged_ok(const fdtd_grid *g) {
+  if (const char *e = getenv("FDTDMOR_MARCH_TMA")) return atoi(e) != 0 && encode_fn() != nullptr;
+  return g->prec == FDTD_F32 && g->nx % 4 == 0 && (g->nx * g->id_bytes) % 16 == 0 && encode_fn() != nullptr;
+}
+
+template <typename ID>
+static fdtd_status march_maps(fdtd_grid *g, const MarchMaps **out) {
+  static thread_local MarchMapCache cache;
+  if (cache.f0 != g->fields[0].ptr || cache.f1 != g->fields[1].ptr || cache.emat != g->emat.ptr || cache.nc != g->nc) {
+    using St = MarchStage<ID>;
+    for (int b = 0; b < 2; ++b) {
+      char *base = static_cast<char *>(g->fields[b].ptr);
+      for (int c = 0; c < 3; ++c) {
+        FDTD_CHECK(make_map(&cache.maps[b].E[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base + (size_t)c * g->nc * 4, g,
+                            St::EX, St::EY));
+        FDTD_CHECK(make_map(&cache.maps[b].H[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base + (size_t)(3 + c) * g->nc * 4,
+                            g, St::HX, St::HY));
+      }
+      FDTD_CHECK(make_map(&cache.maps[b].M, sizeof(ID) == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                          (int)sizeof(ID), g->emat.ptr, g, St::MX, St::MY));
+    }
+    cache.f0 = g->fields[0].ptr; cache.f1 = g->fields[1].ptr; cache.emat = g->emat.ptr; cache.nc = g->nc;
+  }
+  *out = &cache.maps[g->cur];
+  return FDTD_OK;
+}
+
+template <typename T, typename ID, bool HH, int VW, int MTY, bool STAGED>
+static fdtd_status launch_march_main(fdtd_grid *g, const YeeArgs<T, ID> &a, cudaStream_t s) {
+  auto kern = yee_march_kernel<T, ID, HH, VW, MTY, STAGED>;
+  const size_t smem = STAGED ? MarchStage<ID>::SMEM : 0;
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (STAGED) FDTD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDTD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LTX * MTY, smem));
+    per_sm = std::max(1, per_sm);
+  }
+  const int ntx = (g->nx + LTX * VW - 1) / (LTX * VW), nty = (g->ny + MTY - 2) / (MTY - 1);
+  const char *lz_env = getenv("FDTDMOR_LZ");
+  const int lz = std::min(g->nz, lz_env ? env_int("FDTDMOR_LZ", 16) : choose_kchunk(g, ntx * nty, per_sm));
+  const dim3 grid(ntx, nty, (g->nz + lz - 1) / lz);
+  MarchMaps none_maps;
+  memset(&none_maps, 0, sizeof(none_maps));
+  const MarchMaps *mp = &none_maps;
+  if (STAGED) FDTD_CHECK(march_maps<ID>(g, &mp));
+  FDTD_CHECK_CUDA(launch_dependent_smem(kern, grid, dim3(LTX, MTY), smem, s, a, g->emat.as<ID>(), lz, *mp,
+                                        g->errflag.as<unsigned>()));
+  return FDTD_OK;
+}
+
 template <typename T, typename ID, bool HH, int VW, int MTY>
 static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, cudaStream_t s) {
   FDTD_CHECK(ensure_emat<ID>(g, s));
@@ -398,16 +586,12 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
   YeeArgs<T, ID> a = split_args<T, ID>(g);
   a.u = static_cast<const T *>(u_row);
   a.y = static_cast<T *>(y_row);
-  static int per_sm = 0;
-  if (!per_sm) {
-    FDTD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_march_kernel<T, ID, HH, VW, MTY>, LTX * MTY, 0));
-    per_sm = std::max(1, per_sm);
+  if constexpr (sizeof(T) == 4 && VW == 4 && MTY == 8) {
+    if (march_staged_ok(g)) FDTD_CHECK((launch_march_main<T, ID, HH, VW, MTY, true>(g, a, s)));
+    else FDTD_CHECK((launch_march_main<T, ID, HH, VW, MTY, false>(g, a, s)));
+  } else {
+    FDTD_CHECK((launch_march_main<T, ID, HH, VW, MTY, false>(g, a, s)));
   }
-  const int ntx = (g->nx + LTX * VW - 1) / (LTX * VW), nty = (g->ny + MTY - 2) / (MTY - 1);
-  const char *lz_env = getenv("FDTDMOR_LZ");
-  const int lz = std::min(g->nz, lz_env ? env_int("FDTDMOR_LZ", 16) : choose_kchunk(g, ntx * nty, per_sm));
-  const dim3 grid(ntx, nty, (g->nz + lz - 1) / lz);
-  FDTD_CHECK_CUDA(launch_dependent(yee_march_kernel<T, ID, HH, VW, MTY>, grid, dim3(LTX, MTY), s, a, g->emat.as<ID>(), lz));
   FDTD_CHECK(after_launch("yee_march_kernel"));
   if (g->nflat_src) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_src_kernel<T, ID, HH>, dim3((g->nflat_src + 127) / 128), dim3(128), s, a,

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "grid_internal.cuh"
 #include "yee_internal.cuh"
+#include "tma_util.cuh"
 
 namespace fdtdmor {
 
@@ -54,41 +55,6 @@ struct QMaps {
   CUtensorMap H[2][3];
   CUtensorMap M;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait on the given phase parity; false when the limit is reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // Material of every cell an E or H coefficient of tile t at plane k can see
 // (x in [i0-1, i0+32], y in [j0-1, j0+7], z in {k-1, k}), or -1 if they differ.
@@ -339,41 +305,6 @@ __global__ void __launch_bounds__(QNT, sizeof(T) == 4 ? 3 : 1) yee_tma_kernel(co
 }
 
 // ------------------------------------------------------------------ host
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
-static fdtd_status make_map(CUtensorMap *m, CUtensorMapDataType dt, int elem, void *base, const fdtd_grid *g,
-                            int bx, int by) {
-  EncodeTiledFn fn = encode_fn();
-  FDTD_REQUIRE(fn, "cuTensorMapEncodeTiled is not available");
-  cuuint64_t dims[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
-  cuuint64_t strides[2] = {(cuuint64_t)g->nx * elem, (cuuint64_t)g->nx * g->ny * elem};
-  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return FDTD_ECUDA;
-  }
-  return FDTD_OK;
-}
-
 void yee_tma_tile(int *tx, int *ty) {
   *tx = QTX;
   *ty = QTY;

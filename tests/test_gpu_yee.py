@@ -275,3 +275,27 @@ def test_edge_coefficient_map_is_bit_exact(monkeypatch, prec):
         else:
             assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
     assert np.max(np.abs(out["1"][0] - out["1"][1])) > 1e-3 * np.abs(out["1"][0]).max()
+
+
+@pytest.mark.parametrize("staged", ["1", "0"])
+@pytest.mark.parametrize("many", [False, True])
+@pytest.mark.parametrize("nx", [48, 272])
+def test_march_four_cells_per_thread(monkeypatch, staged, many, nx):
+    """The fused one-pass form with 4 FP32 cells per thread, its plane inputs
+    staged through shared memory by TMA or loaded per thread: parity with the
+    oracle on one tile (nx = 48) and on three tiles with a ragged last one
+    (nx = 272: +x halo columns between tiles), uint8 and uint16 ids."""
+    monkeypatch.setenv("FDTDMOR_MARCH_VW", "4")
+    monkeypatch.setenv("FDTDMOR_MARCH_TMA", staged)
+    grid = ragged_grid(nx=nx, ny=13, nz=9, many_materials=many)
+    dt = 0.95 * yee.cfl_dt(grid)
+    u = drive(grid, dt, 120)
+    g, yg, fg = _run_gpu(grid, "f32", dt, u, kernel="march")
+    g.check()
+    s, yo, fo = _run_oracle(grid, dt, u)
+    for c in range(6):
+        assert _rel(fg[c], fo[c]) <= 1e-4, c
+    assert _rel(yg, yo) <= TOL_F32_PROBE
+    for c in range(3):
+        assert np.all(fg[c][~s.e_mask[c]] == 0)
+        assert np.all(fg[3 + c][~s.h_mask[c]] == 0)
