@@ -133,8 +133,11 @@ FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
  * 7 rows, each thread updating VW consecutive x cells (4 in FP32 on wide
  * grids) with H one plane behind E; the rows exchange E through shared memory
  * (one barrier per plane) and the tile's first row above and +x column are
- * recomputed; sources and probes follow in two small launches (the step is
- * linear). */
+ * recomputed; in FP32 with 4 cells per thread the plane inputs are staged in
+ * shared memory by TMA three planes ahead (rows of the fields and of the
+ * material map 16-byte aligned: nx a multiple of 4, and of 16 with uint8
+ * material ids); sources and probes follow in two small launches (the step
+ * is linear).  A staged wait that gives up sets the flag fdtd_check reports. */
 typedef enum {
   FDTD_KERNEL_AUTO = 0,
   FDTD_KERNEL_PERSIST = 1,

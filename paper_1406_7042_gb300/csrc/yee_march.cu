@@ -14,6 +14,10 @@
 // The new state goes to the other buffer (ping-pong), so neighbours always
 // read the old one.
 //
+// In FP32 with 4 cells per thread the plane inputs (H with the row below and
+// the columns either side, E and the material map with the +x column) are
+// staged in shared memory by TMA, three planes ahead of the plane in work.
+//
 // DRAM sees each field value read once and written once per step (the 48 B
 // per cell of the fused form, plus the material map); the halo row's and
 // chunk tops' reads come mostly from L2.  Sources and probes are applied
