@@ -525,11 +525,17 @@ static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   return FDTD_OK;
 }
 
-// Tensor maps of the staged form for both state buffers of the last grid used.
+// Tensor maps of the staged form for both state buffers of the last grid
+// used, keyed on everything they encode (a later grid may reuse the same
+// device addresses with other sizes or id width).
 struct MarchMapCache {
   MarchMaps maps[2];
   const void *f0 = nullptr, *f1 = nullptr, *emat = nullptr;
-  int64_t nc = 0;
+  int nx = 0, ny = 0, nz = 0, id_bytes = 0;
+  bool same(const fdtd_grid *g) const {
+    return f0 == g->fields[0].ptr && f1 == g->fields[1].ptr && emat == g->emat.ptr && nx == g->nx && ny == g->ny &&
+           nz == g->nz && id_bytes == g->id_bytes;
+  }
 };
 
 // The staged form needs 16-byte rows of the fields and of the material map.
@@ -541,7 +547,7 @@ static bool march_staged_ok(const fdtd_grid *g) {
 template <typename ID>
 static fdtd_status march_maps(fdtd_grid *g, const MarchMaps **out) {
   static thread_local MarchMapCache cache;
-  if (cache.f0 != g->fields[0].ptr || cache.f1 != g->fields[1].ptr || cache.emat != g->emat.ptr || cache.nc != g->nc) {
+  if (!cache.same(g)) {
     using St = MarchStage<ID>;
     for (int b = 0; b < 2; ++b) {
       char *base = static_cast<char *>(g->fields[b].ptr);
@@ -554,7 +560,8 @@ static fdtd_status march_maps(fdtd_grid *g, const MarchMaps **out) {
       FDTD_CHECK(make_map(&cache.maps[b].M, sizeof(ID) == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
                           (int)sizeof(ID), g->emat.ptr, g, St::MX, St::MY));
     }
-    cache.f0 = g->fields[0].ptr; cache.f1 = g->fields[1].ptr; cache.emat = g->emat.ptr; cache.nc = g->nc;
+    cache.f0 = g->fields[0].ptr; cache.f1 = g->fields[1].ptr; cache.emat = g->emat.ptr;
+    cache.nx = g->nx; cache.ny = g->ny; cache.nz = g->nz; cache.id_bytes = g->id_bytes;
   }
   *out = &cache.maps[g->cur];
   return FDTD_OK;

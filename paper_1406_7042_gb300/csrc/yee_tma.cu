@@ -316,9 +316,20 @@ bool yee_tma_eligible(const fdtd_grid *g) {
   return g->nx % need == 0 && encode_fn() != nullptr;
 }
 
+// Tensor maps of the last grid used, with everything they encode: a later
+// grid may reuse the same device addresses with other sizes or types.
 struct TmaCache {
   QMaps maps;
   const void *f0 = nullptr, *f1 = nullptr, *mat = nullptr;
+  int nx = 0, ny = 0, nz = 0, elem = 0, id_bytes = 0;
+  bool same(const fdtd_grid *g) const {
+    return f0 == g->fields[0].ptr && f1 == g->fields[1].ptr && mat == g->mat.ptr && nx == g->nx && ny == g->ny &&
+           nz == g->nz && elem == g->elem && id_bytes == g->id_bytes;
+  }
+  void set(const fdtd_grid *g) {
+    f0 = g->fields[0].ptr; f1 = g->fields[1].ptr; mat = g->mat.ptr;
+    nx = g->nx; ny = g->ny; nz = g->nz; elem = g->elem; id_bytes = g->id_bytes;
+  }
 };
 
 template <typename T, typename ID, bool HH>
@@ -359,7 +370,7 @@ static fdtd_status launch_tma_t(fdtd_grid *g, const void *u_row, void *y_row, in
 fdtd_status launch_yee_tma(fdtd_grid *g, const void *u_row, void *y_row, int kchunk, cudaStream_t s) {
   static thread_local TmaCache cache;  // tensor maps of the last grid (rebuilt when its buffers change)
   const bool f64 = g->prec == FDTD_F64;
-  if (cache.f0 != g->fields[0].ptr || cache.f1 != g->fields[1].ptr || cache.mat != g->mat.ptr) {
+  if (!cache.same(g)) {
     const CUtensorMapDataType ft = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const int el = g->elem;
     for (int b = 0; b < 2; ++b) {
@@ -373,7 +384,7 @@ fdtd_status launch_yee_tma(fdtd_grid *g, const void *u_row, void *y_row, int kch
       FDTD_CHECK(make_map(&cache.maps.M, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g->mat.ptr, g, QTX + 32, QTY + 2));
     else
       FDTD_CHECK(make_map(&cache.maps.M, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g->mat.ptr, g, QTX + 16, QTY + 2));
-    cache.f0 = g->fields[0].ptr; cache.f1 = g->fields[1].ptr; cache.mat = g->mat.ptr;
+    cache.set(g);
   }
   unsigned *err = g->errflag.as<unsigned>();
   if (!g->uflag_ready) {

@@ -299,3 +299,27 @@ def test_march_four_cells_per_thread(monkeypatch, staged, many, nx):
     for c in range(3):
         assert np.all(fg[c][~s.e_mask[c]] == 0)
         assert np.all(fg[3 + c][~s.h_mask[c]] == 0)
+
+
+@pytest.mark.parametrize("kernel", ["march", "tma"])
+def test_tensor_maps_follow_a_new_grid_at_reused_addresses(monkeypatch, kernel):
+    """The TMA-fed forms cache their tensor maps per grid; a second grid with
+    the same cell count (so the allocator hands back the same device blocks)
+    but other row lengths must get maps of its own shape."""
+    monkeypatch.setenv("FDTDMOR_MARCH_VW", "4")
+    monkeypatch.setenv("FDTDMOR_MARCH_TMA", "1")
+    first = ragged_grid(nx=48, ny=26, nz=9, seed=81)
+    dt1 = 0.95 * yee.cfl_dt(first)
+    g1, _, _ = _run_gpu(first, "f32", dt1, drive(first, dt1, 40), kernel=kernel)
+    g1.check()
+    g1.close()
+    del g1
+    second = ragged_grid(nx=96, ny=13, nz=9, seed=82)
+    dt = 0.95 * yee.cfl_dt(second)
+    u = drive(second, dt, 100)
+    g, yg, fg = _run_gpu(second, "f32", dt, u, kernel=kernel)
+    g.check()
+    _, yo, fo = _run_oracle(second, dt, u)
+    for c in range(6):
+        assert _rel(fg[c], fo[c]) <= 1e-4, c
+    assert _rel(yg, yo) <= TOL_F32_PROBE
