@@ -236,6 +236,18 @@ FDTD_API fdtd_status fdtd_resonances(const void *y, int64_t nsteps, int p, fdtd_
                             double fmax, int nf, int hann, double rel_floor, int npk, double *peaks_hz,
                             int *nfound, fdtd_stream_t stream);
 
+/* S-parameters from port waveforms (Sec. V-D): with Y the spectra of y (the
+ * structure driven at probe port_in) and Yi those of y_inc (a reference run
+ * carrying only the incident wave, e.g. the structure replaced by a matched
+ * line), S_q(f) = (Y_q - [q = port_in] Yi_q) / Yi_port_in: S11 at the driven
+ * port (reflected over incident), transmission elsewhere.  y, y_inc: device
+ * [nsteps][p] of type prec; freqs: host [nf]; out: host [p][nf][2] (re, im),
+ * FP64.  FDTD_EINVAL when the incident spectrum is exactly zero at a
+ * requested frequency.  Synchronises the stream. */
+FDTD_API fdtd_status fdtd_sparams(const void *y, const void *y_inc, int64_t nsteps, int p, fdtd_prec prec, double dt,
+                         int nf, const double *freqs, int hann, int port_in, double *out,
+                         fdtd_stream_t stream);
+
 /* Kernel launches issued by the calling thread since the last reset (for
  * launch accounting).  fdtd_launch_count(1) returns the count and resets it. */
 FDTD_API int64_t fdtd_launch_count(int reset);

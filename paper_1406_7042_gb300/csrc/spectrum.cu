@@ -1,11 +1,12 @@
 // Frequency-domain post-processing of probe waveforms: discrete Fourier
-// transform at chosen frequencies and resonance extraction (the spectra from
-// which the paper reads its resonance frequencies, Sec. V-A, and S-parameters,
-// Sec. V-D).  Y_p(f) = sum_n w_n y^n_p exp(-j 2 pi f t_n) dt with
+// transform at chosen frequencies, resonance extraction and S-parameters (the
+// spectra from which the paper reads its resonance frequencies, Sec. V-A, and
+// S11, S21, Sec. V-D).  Y_p(f) = sum_n w_n y^n_p exp(-j 2 pi f t_n) dt with
 // t_n = (n + 1) dt (y^n samples E^{n+1}) and the optional Hann window
 // w_n = sin^2(pi (n + 1/2) / N).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <vector>
 
 #include "common.cuh"
@@ -87,6 +88,30 @@ fdtd_status fdtd_dft(const void *y, int64_t nsteps, int p, fdtd_prec prec, doubl
   FDTD_REQUIRE(nsteps >= 1 && p >= 1 && p <= 65535 && nf >= 1 && dt > 0, "fdtd_dft: bad sizes");
   FDTD_REQUIRE(prec == FDTD_F32 || prec == FDTD_F64, "fdtd_dft: prec must be FDTD_F32 or FDTD_F64");
   return dft_host(y, nsteps, p, prec, dt, nf, freqs, hann, out, (cudaStream_t)stream);
+}
+
+fdtd_status fdtd_sparams(const void *y, const void *y_inc, int64_t nsteps, int p, fdtd_prec prec, double dt, int nf,
+                         const double *freqs, int hann, int port_in, double *out, fdtd_stream_t stream) {
+  FDTD_REQUIRE(y && y_inc && freqs && out, "fdtd_sparams: NULL argument");
+  FDTD_REQUIRE(p >= 1 && port_in >= 0 && port_in < p, "fdtd_sparams: port_in must be in [0, p)");
+  FDTD_REQUIRE(nf >= 1, "fdtd_sparams: nf must be >= 1");
+  std::vector<double> Y(2 * (size_t)nf * p), Yi(2 * (size_t)nf * p);
+  FDTD_CHECK(fdtd_dft(y, nsteps, p, prec, dt, nf, freqs, hann, Y.data(), stream));
+  FDTD_CHECK(fdtd_dft(y_inc, nsteps, p, prec, dt, nf, freqs, hann, Yi.data(), stream));
+  for (int i = 0; i < nf; ++i) {
+    const size_t ii = ((size_t)port_in * nf + i) * 2;
+    const std::complex<double> inc(Yi[ii], Yi[ii + 1]);
+    FDTD_REQUIRE(std::abs(inc) > 0, "fdtd_sparams: the incident spectrum vanishes at frequency %d", i);
+    for (int q = 0; q < p; ++q) {
+      const size_t k = ((size_t)q * nf + i) * 2;
+      std::complex<double> num(Y[k], Y[k + 1]);
+      if (q == port_in) num -= inc;
+      const std::complex<double> sq = num / inc;
+      out[k] = sq.real();
+      out[k + 1] = sq.imag();
+    }
+  }
+  return FDTD_OK;
 }
 
 fdtd_status fdtd_resonances(const void *y, int64_t nsteps, int p, fdtd_prec prec, double dt, double fmin,

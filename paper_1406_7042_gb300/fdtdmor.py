@@ -100,6 +100,8 @@ _SIGS = [
     ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
     ("fdtd_dft", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                            C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    ("fdtd_sparams", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int,
+                               C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     ("fdtd_resonances", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                   C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.c_void_p]),
@@ -524,6 +526,23 @@ def dft(y, dt: float, freqs, hann: bool = False, stream=None) -> np.ndarray:
     check(lib().fdtd_dft(_dptr(y), int(y.shape[0]), int(y.shape[1]), prec, float(dt), int(f.size),
                          f.ctypes.data_as(C.POINTER(C.c_double)), 1 if hann else 0,
                          out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def sparams(y, y_inc, dt: float, freqs, port_in: int = 0, hann: bool = False, stream=None) -> np.ndarray:
+    """(p, nf) complex S-parameters of the probes against the incident wave of a
+    reference run (fdtd_sparams); y and y_inc: device (nsteps, p), same type."""
+    import torch
+    y = y.contiguous()
+    y_inc = y_inc.to(y.dtype).contiguous()
+    if tuple(y_inc.shape) != tuple(y.shape):
+        raise ValueError("y_inc must have the shape of y")
+    f = np.ascontiguousarray(np.asarray(freqs, np.float64))
+    out = np.zeros((y.shape[1], f.size, 2), np.float64)
+    prec = FDTD_F64 if y.dtype == torch.float64 else FDTD_F32
+    check(lib().fdtd_sparams(_dptr(y), _dptr(y_inc), int(y.shape[0]), int(y.shape[1]), prec, float(dt), int(f.size),
+                             f.ctypes.data_as(C.POINTER(C.c_double)), 1 if hann else 0, int(port_in),
+                             out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
     return out[..., 0] + 1j * out[..., 1]
 
 

@@ -44,3 +44,32 @@ def test_demo_cavity_resonances_on_gpu():
     pko = spectrum.resonances(y.cpu().numpy(), dt, 0.15e9, 0.30e9, nf=3000, rel_floor=0.05)
     assert pk.size == 2 and np.allclose(pk, pko, rtol=1e-9)
     assert np.all(np.abs(pk / 1e9 - d["resonances_ghz"]) / d["resonances_ghz"] < 0.01)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 1e-6)])
+def test_sparams_match_oracle_and_closed_form(dtype, tol):
+    """fdtd_sparams against the oracle on random waveforms, and on a delayed,
+    scaled reflection and transmission of a pulse against r exp(-j 2 pi f d)
+    and a exp(-j 2 pi f e)."""
+    npd = np.float64 if dtype == torch.float64 else np.float32
+    rng = np.random.default_rng(9)
+    N, p, dt = 3000, 3, 1e-12
+    y = rng.standard_normal((N, p)).astype(npd)
+    yi = rng.standard_normal((N, p)).astype(npd)
+    f = np.linspace(2e9, 40e9, 65)
+    got = F.sparams(torch.tensor(y, device="cuda"), torch.tensor(yi, device="cuda"), dt, f, port_in=1)
+    ref = spectrum.sparams(y.astype(np.float64), yi.astype(np.float64), dt, f, port_in=1)
+    # same input values on both sides (FP64 sums): agreement to rounding
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.abs(ref).max()
+    t = (np.arange(N) + 1) * dt
+    x = np.exp(-((t - 0.4e-9) * np.pi * 8e9) ** 2) * np.sin(2 * np.pi * 12e9 * (t - 0.4e-9))
+    d, e, r, a = 500, 300, -0.4, 0.75
+    yinc = np.zeros((N, 2)); yinc[:, 0] = x
+    ys = yinc.copy(); ys[d:, 0] += r * x[:N - d]; ys[e:, 1] = a * x[:N - e]
+    f = np.linspace(6e9, 18e9, 25)
+    S = F.sparams(torch.tensor(ys.astype(npd), device="cuda"), torch.tensor(yinc.astype(npd), device="cuda"), dt, f)
+    # closed forms up to the rounding of r x, a x in the waveform type
+    assert np.max(np.abs(S[0] - r * np.exp(-2j * np.pi * f * d * dt))) <= tol
+    assert np.max(np.abs(S[1] - a * np.exp(-2j * np.pi * f * e * dt))) <= tol
+    with pytest.raises(F.FdtdError):
+        F.sparams(torch.tensor(ys, device="cuda"), torch.zeros((N, 2), dtype=torch.float64, device="cuda"), dt, f)
