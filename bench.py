@@ -80,7 +80,7 @@ class Clocks:
 
 def _workload():
     from paper_1406_7042_gb300 import workloads as W
-    return W.config2()
+    return W.graded_cavity_workload()
 
 
 def run_reference(args):
@@ -396,7 +396,7 @@ def precision_study(F, W, absorbing=False):
     s = 0.99 against the FP64 full-order run of the same grid (PEC box, or
     with the paper's matched absorber on five faces)."""
     import torch
-    wl = W.config4(downscale=True, absorbing=absorbing)
+    wl = W.microstrip_workload(downscale=True, absorbing=absorbing)
     g = wl.grid
     ref = F.Grid(g, "f64")
     dt0 = wl.s_ref * ref.cfl_dt()
@@ -463,7 +463,7 @@ def accuracy_sweep(F, W, wl, grid, model, yref, dt0, nref):
 def hbm_grid_measure(F, W, hbm, nsteps=200):
     """Yee kernel alone on the 384x384x64 metascreen grid (453 MB state, HBM-bound)."""
     import torch
-    wl = W.config5()
+    wl = W.metascreen_workload()
     g = wl.grid
     grid = F.Grid(g, "f32")
     dt = wl.s_ref * grid.cfl_dt()
@@ -490,7 +490,7 @@ def only_yee(args):
     import torch
     from paper_1406_7042_gb300 import fdtdmor as F
     from paper_1406_7042_gb300 import workloads as W
-    wl = {"graded": W.config2, "metascreen": W.config5, "cavity10": W.config1}[args.only_yee]()
+    wl = {"graded": W.graded_cavity_workload, "metascreen": W.metascreen_workload, "cavity10": W.cavity10_workload}[args.only_yee]()
     prec = "f64" if wl.precision == "f64" else "f32"
     grid = F.Grid(wl.grid, prec)
     dt = wl.s_ref * grid.cfl_dt()

@@ -211,7 +211,7 @@ def _distinct_cell(rng, used: set, dims, margin: int = 2):
     return c
 
 
-# ---------------------------------------------------------------- config 1
+# ---------------------------------------------------------------- 10^3 PEC cavity
 def cavity_uniform(n: int = 10, d: float = 1e-3, seed: int = SEED_BASE + 1,
                    nports: int = 1, nprobes: int = 1) -> GridSpec:
     """Lossless vacuum PEC cube of n^3 cells of size d, Ez point ports/probes."""
@@ -227,14 +227,14 @@ def cavity_uniform(n: int = 10, d: float = 1e-3, seed: int = SEED_BASE + 1,
     return g
 
 
-def config1(seed: int = SEED_BASE + 1) -> Workload:
+def cavity10_workload(seed: int = SEED_BASE + 1) -> Workload:
     g = cavity_uniform(10, 1e-3, seed)
     return Workload("cavity10_f64", g, 0.99, 4000, 10e9, 10e9, q=40, L=2, M=1.1,
                     fmax=15e9, s_red=[0.99, 4.95, 9.9], nsteps_red=[4000, 800, 400],
                     precision="f64")
 
 
-# ---------------------------------------------------------------- config 2
+# ---------------------------------------------------------------- graded cavity
 def graded_z(n_total: int = 64, coarse: float = 0.5e-3, fine: float = 0.05e-3,
              n_grade: int = 8, n_slab: int = 2) -> np.ndarray:
     """z spacings: coarse cells, a geometric grading over n_grade cells down to
@@ -273,7 +273,7 @@ def cavity_graded(n: int = 64, seed: int = SEED_BASE + 2, nblocks: int = 16,
     return g
 
 
-def config2(seed: int = SEED_BASE + 2, n: int = 64) -> Workload:
+def graded_cavity_workload(seed: int = SEED_BASE + 2, n: int = 64) -> Workload:
     """64^3 graded cavity.  Its 0.163 ps step puts the whole 5-15 GHz band on an
     arc of 2 pi fmax dt0 = 0.0154 rad of the unit circle, so the expansion
     radius is taken as 1 + pi fmax dt0 = 1.0077 (half that arc away from the
@@ -283,7 +283,7 @@ def config2(seed: int = SEED_BASE + 2, n: int = 64) -> Workload:
                     M=1.0077, fmax=15e9, s_red=[19.8], nsteps_red=[20000], precision="f32")
 
 
-# ---------------------------------------------------------------- config 3
+# ---------------------------------------------------------------- waveguide and cavity batch
 def waveguide_iris(seed: int = SEED_BASE + 3, nx: int = 256, ny: int = 64, nz: int = 32,
                    d: float = 0.1e-3) -> GridSpec:
     """PEC rectangular guide (broad wall along y) with one seeded iris and two
@@ -327,7 +327,7 @@ def cavity_batch(seed: int = SEED_BASE + 30, count: int = 32, lo: int = 24, hi: 
     return out
 
 
-def config3(seed: int = SEED_BASE + 3, absorbing: bool = False) -> Workload:
+def waveguide_workload(seed: int = SEED_BASE + 3, absorbing: bool = False) -> Workload:
     g = waveguide_iris(seed)
     if absorbing:   # the paper's guide ends on matched absorbers (Sec. V-B)
         g = add_absorber(g, "xX")
@@ -335,7 +335,7 @@ def config3(seed: int = SEED_BASE + 3, absorbing: bool = False) -> Workload:
                     fmax=45e9, s_red=[0.99], nsteps_red=[20000], precision="f32")
 
 
-# ---------------------------------------------------------------- config 4
+# ---------------------------------------------------------------- microstrip filter
 def microstrip(seed: int = SEED_BASE + 4, nx: int = 400, ny: int = 200, nz: int = 24,
                dxy: float = 0.4e-3, dz: float = 0.2e-3, n_sub: int = 6) -> GridSpec:
     """Substrate of n_sub layers (eps_r 9.8) on the PEC ground (z = 0), a
@@ -379,7 +379,7 @@ def microstrip(seed: int = SEED_BASE + 4, nx: int = 400, ny: int = 200, nz: int 
     return g
 
 
-def config4(seed: int = SEED_BASE + 4, downscale: bool = False, absorbing: bool = False) -> Workload:
+def microstrip_workload(seed: int = SEED_BASE + 4, downscale: bool = False, absorbing: bool = False) -> Workload:
     if downscale:
         g = microstrip(seed, 100, 50, 24)
     else:
@@ -391,7 +391,7 @@ def config4(seed: int = SEED_BASE + 4, downscale: bool = False, absorbing: bool 
                     s_red=[0.99, 2.97, 4.95], nsteps_red=[8000, 2667, 1600], precision="f32")
 
 
-# ---------------------------------------------------------------- config 5
+# ---------------------------------------------------------------- focusing metascreen
 def metascreen(seed: int = SEED_BASE + 5, nxy: int = 384, nz: int = 64, d: float = 0.25e-3,
                npix: int = 64, pix_xy: int = 6, pix_z: int = 2) -> GridSpec:
     """Dielectric screen of npix x npix design pixels (pix_xy^2 x pix_z cells
@@ -418,7 +418,7 @@ def metascreen(seed: int = SEED_BASE + 5, nxy: int = 384, nz: int = 64, d: float
     return g
 
 
-def config5(seed: int = SEED_BASE + 5, downscale: bool = False, absorbing: bool = False) -> Workload:
+def metascreen_workload(seed: int = SEED_BASE + 5, downscale: bool = False, absorbing: bool = False) -> Workload:
     if downscale:
         g = metascreen(seed, 48, 16, 0.25e-3, 8, 6, 2)
     else:

@@ -116,7 +116,7 @@ def test_metascreen_downscale_gradient_against_oracle():
     """The 48x48x16 metascreen (8x8 design pixels of 6x6x2 cells) with a
     short broadband pulse: per-pixel FP32 GPU gradient against the FP64
     oracle gradient summed over each pixel's cells."""
-    wl = W.config5(downscale=True)
+    wl = W.metascreen_workload(downscale=True)
     grid = wl.grid
     dt = wl.s_ref * yee.cfl_dt(grid)
     u = W.excitation(grid, 30e9, 60e9, dt, 400)
@@ -132,7 +132,7 @@ def test_metascreen_full_size_central_differences():
     """384x384x64 metascreen, 2048 FP32 steps with the default sqrt(T)
     checkpoints: adjoint per-pixel gradient against central differences
     (relative step 1e-2) of the FP32 forward loss on 16 seeded pixels."""
-    wl = W.config5()
+    wl = W.metascreen_workload()
     grid = wl.grid
     g = F.Grid(grid, "f32")
     dt = wl.s_ref * g.cfl_dt()

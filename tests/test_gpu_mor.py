@@ -66,7 +66,7 @@ def test_edge_props_match_oracle(prec):
 
 @pytest.fixture(scope="module")
 def cav10():
-    wl = W.config1()
+    wl = W.cavity10_workload()
     g = wl.grid
     s = yee.assemble(g)
     dt0 = wl.s_ref * yee.cfl_dt(g)
@@ -329,7 +329,7 @@ def test_full_size_bench_workload_properties():
     20x CFL a reduced step matrix with no eigenvalue outside the unit circle
     (Sec. III-A), checked in FP64 on the host from the projected matrices."""
     from oracle import mor
-    wl = W.config2()
+    wl = W.graded_cavity_workload()
     grid = F.Grid(wl.grid, "f32")
     dt0 = wl.s_ref * grid.cfl_dt()
     b = F.Basis(grid, 20, dt0, wl.L, wl.M, wl.fmax, tol=1e-4, defl_tol=1e-5, allow_noconv=True)
@@ -356,7 +356,7 @@ def test_tensor_core_gram_schmidt_many_blocks(orth):
     vectors, nearly dependent H parts): both halves of the tensor-core CGS2
     basis orthonormal to FP32 level, and D~eps, D~mu positive definite (the
     perturbation factorises them)."""
-    wl = W.config4(downscale=True)
+    wl = W.microstrip_workload(downscale=True)
     grid = F.Grid(wl.grid, "f32")
     dt0 = wl.s_ref * grid.cfl_dt()
     b = F.Basis(grid, 100, dt0, wl.L, wl.M, wl.fmax, tol=1e-5, defl_tol=1e-5, orth=orth, allow_noconv=True)

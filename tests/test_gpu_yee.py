@@ -39,7 +39,7 @@ def _rel(a, b):
 
 
 def test_cfl_matches_oracle():
-    for grid in (W.config1().grid, W.config2().grid, ragged_grid()):
+    for grid in (W.cavity10_workload().grid, W.graded_cavity_workload().grid, ragged_grid()):
         g = F.Grid(grid, "f32")
         assert abs(g.cfl_dt() - yee.cfl_dt(grid)) <= 1e-15 * yee.cfl_dt(grid)
 
@@ -74,8 +74,8 @@ def test_ragged_graded_lossy_parity(prec, many, kernel, nx):
         assert np.all(fg[3 + c][~s.h_mask[c]] == 0)
 
 
-def test_config1_f64_full_run():
-    wl = W.config1()
+def test_cavity10_f64_full_run():
+    wl = W.cavity10_workload()
     dt = wl.s_ref * yee.cfl_dt(wl.grid)
     u = W.excitation(wl.grid, wl.f0, wl.bw, dt, wl.nsteps_ref)
     _, yg, fg = _run_gpu(wl.grid, "f64", dt, u)
@@ -211,7 +211,7 @@ def _light_cone_check(grid, prec, dt, nsteps, centres, half):
 
 
 def test_full_size_graded_cavity_light_cone():
-    wl = W.config2()
+    wl = W.graded_cavity_workload()
     grid = wl.grid
     dt = wl.s_ref * yee.cfl_dt(grid)
     p = grid.ports[0]
@@ -220,7 +220,7 @@ def test_full_size_graded_cavity_light_cone():
 
 
 def test_full_size_metascreen_light_cone():
-    wl = W.config5()
+    wl = W.metascreen_workload()
     grid = wl.grid
     dt = wl.s_ref * yee.cfl_dt(grid)
     centres = [(192, 192, 9), (70, 300, 31), (383 - 5, 5, 8)]
@@ -232,7 +232,7 @@ def test_absorbing_microstrip_parity(prec, tol):
     """The 100x50x24 microstrip with the matched absorber on five faces
     (graded sigma_e and sigma_m, uint8 ids): whole fields and probes against
     the oracle."""
-    wl = W.config4(downscale=True, absorbing=True)
+    wl = W.microstrip_workload(downscale=True, absorbing=True)
     grid = wl.grid
     dt = wl.s_ref * yee.cfl_dt(grid)
     u = W.excitation(grid, wl.f0, wl.bw, dt, 300)

@@ -17,7 +17,7 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_v
 
 @pytest.fixture(scope="module")
 def cav10():
-    wl = W.config1()
+    wl = W.cavity10_workload()
     s = yee.assemble(wl.grid)
     dt0 = wl.s_ref * yee.cfl_dt(wl.grid)
     b = mor.sprim_basis(s, dt0, wl.q, wl.L, wl.M, wl.fmax)
@@ -222,7 +222,7 @@ def test_reduced_run_matches_fdtd_and_converges_in_q():
     assert mor.rel_l2(mor.reduced_run(full, dt0, u), yref) < 1e-10
 
 
-def test_config1_reduced_error_small(cav10):
+def test_cavity10_reduced_error_small(cav10):
     wl, s, dt0, b, red = cav10
     u = W.excitation(wl.grid, wl.f0, wl.bw, dt0, wl.nsteps_ref)
     yref, _, _ = yee.Stepper(s, dt0).run(u)
