@@ -182,8 +182,7 @@ def run_ours(args):
         grid.step(dt0, u, y, reset=True)
         e[1].record(stream)
         if args.mor:
-            basis = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=args.tol, defl_tol=args.defl_tol,
-                            allow_noconv=True)
+            basis = F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=args.tol, defl_tol=args.defl_tol)
             e[2].record(stream)
             model = F.Model(grid, basis)
             e[3].record(stream)
@@ -290,15 +289,15 @@ def run_ours(args):
     return 0
 
 
-def schur_roofline(F, wl, grid, dt0, hbm, peak_src, reps=50):
-    """The shifted Schur-complement operator (h_from_e_kernel + e_from_h_kernel,
-    the pair that dominates the basis build and so the bench step) on the
-    bench grid, all expansion points at once, timed with CUDA events on the
-    launching stream.  Algorithmic bytes per cell and right-hand side: read x
-    (24 B), write and read the H-part intermediate (48 B), read x again and
-    write y (48 B); plus the four per-edge property arrays (48 B per cell)."""
+def schur_roofline(F, wl, grid, dt0, hbm, peak_src, reps=50, id_bytes=1):
+    """The shifted Schur-complement operator S(z) x = a11 x + z curlH(curlE(x)/a22)
+    (one fused pass, schur_fused_kernel, the operator apply of every COCG
+    iteration) on a workload grid, all expansion points at once, timed with
+    CUDA events on the launching stream.  Algorithmic bytes per cell: for each
+    right-hand side read x and write y (complex FP32 E: 2 x 24 B), plus the
+    material id; the kernel's per-edge property reads (48 B per cell, shared by
+    the right-hand sides) are not algorithmic."""
     import torch
-    # expansion points z_l = M exp(j 2 pi (l/L) fmax dt0), l = 0..L (conjugates implied)
     ls = range(0, wl.L + 1) if wl.include_center else [wl.L]
     zs = [wl.M * np.exp(2j * np.pi * (l / max(wl.L, 1)) * wl.fmax * dt0) for l in ls]
     nb = len(zs)
@@ -315,16 +314,28 @@ def schur_roofline(F, wl, grid, dt0, hbm, peak_src, reps=50):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
-    byts = g.ncells * (120.0 * nb + 48.0)
+    byts = g.ncells * (48.0 * nb + id_bytes)
     ach = byts / (ms / 1e3) / 1e9
-    # DRAM bytes per launch of the pair from one ncu capture of `bench.py
-    # --only-schur` (dram__bytes_read.sum + dram__bytes_write.sum of both kernels)
-    traffic = 25164032 + 0 + 43603712 + 11520
-    return {"kernel": "h_from_e_kernel + e_from_h_kernel (Schur-complement apply, mor_schur_apply)", "bound": "hbm",
-            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
-            "peak_source": peak_src, "rhs": nb, "ms_per_launch": round(ms, 4),
+    return {"kernel": "schur_fused_kernel (one-pass Schur-complement apply, mor_schur_apply)", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+            "peak_source": peak_src, "rhs": nb, "grid": [g.nx, g.ny, g.nz], "ms_per_launch": round(ms, 4),
             "bytes_per_launch": int(byts),
-            "note": "dominant kernel pair of the step (basis build); 64^3 blocks of complex RHS, one per expansion point"}
+            "bytes_rule": f"per cell: 48 B per right-hand side (x read, y written, complex FP32 E) + {id_bytes} B material id"}
+
+
+def schur_hbm_measure(F, W, hbm, peak_src):
+    """The fused Schur apply on the 384x384x64 metascreen grid (9.4 M cells,
+    three right-hand sides: 1.36 GB in and out, HBM-bound)."""
+    wl = W.metascreen_workload()
+    grid = F.Grid(wl.grid, "f32")
+    dt0 = wl.s_ref * grid.cfl_dt()
+
+    from types import SimpleNamespace
+    # the bench cavity's expansion arc (L = 2, fmax = 15 GHz, M = 1 + pi fmax dt0) on this grid's dt
+    pts = SimpleNamespace(grid=wl.grid, L=2, M=1.0 + np.pi * 15e9 * dt0, fmax=15e9, include_center=True)
+    out = schur_roofline(F, pts, grid, dt0, hbm, peak_src, reps=10, id_bytes=2)
+    grid.close()
+    return out
 
 
 def batch_measure(F, W, nsteps=200):
@@ -568,12 +579,14 @@ def main():
         print(json.dumps({"only_gram": "tf32 and bf16 V^T V, n = 786432, q = 200"}))
         return 0
     if args.only_schur:
-        import torch
         from paper_1406_7042_gb300 import fdtdmor as F
+        from paper_1406_7042_gb300 import workloads as W
         wl = _workload()
         grid = F.Grid(wl.grid, "f32")
         dt0 = wl.s_ref * grid.cfl_dt()
-        print(json.dumps({"only_schur": schur_roofline(F, wl, grid, dt0, _peaks().get("hbm_gbs", 6800.0), "", reps=20)}))
+        hb = _peaks().get("hbm_gbs", 6800.0)
+        print(json.dumps({"only_schur": schur_roofline(F, wl, grid, dt0, hb, "", reps=20),
+                          "only_schur_hbm": schur_hbm_measure(F, W, hb, "")}))
         return 0
     if args.only_tensor:
         from paper_1406_7042_gb300 import fdtdmor as F

@@ -288,13 +288,21 @@ FDTD_API fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda,
                      int N, const float *w, double *G, fdtd_stream_t stream);
 
 /* Krylov solver of the shifted Schur-complement systems.  The paper uses
- * conjugate gradient squared (Sec. IV-B).  AUTO picks it for FDTD_F64 grids
- * and BiCGSTAB for FDTD_F32 grids, where the squared residual polynomial of
- * CGS amplifies rounding on the complex-shifted (indefinite) systems.  Both
- * are right-preconditioned by the Jacobi diagonal, and convergence is
- * confirmed on the true residual b - S x, with restarts when the recursively
- * updated residual has drifted from it. */
-typedef enum { MOR_SOLVER_AUTO = 0, MOR_SOLVER_CGS = 1, MOR_SOLVER_BICGSTAB = 2 } mor_solver;
+ * conjugate gradient squared (Sec. IV-B); AUTO picks it for FDTD_F64 grids.
+ * CGS and BiCGSTAB are right-preconditioned by the Jacobi diagonal, and
+ * convergence is confirmed on the true residual b - S x, with restarts when
+ * the recursively updated residual has drifted from it.
+ * MOR_SOLVER_COCG (AUTO for FDTD_F32 grids): the Schur complement is complex
+ * symmetric, so the conjugate-orthogonal CG applies -- one operator apply per
+ * iteration -- with the unconjugated volume-weighted product and the Jacobi
+ * diagonal plus one damped Jacobi step on the nodal operator
+ * G^T diag(V a11) G for the gradient fields the curl-curl part annihilates.
+ * It runs inside an FP64 refinement loop: the true residual bhat - S x is
+ * formed in FP64 from an FP64 solution, and the inner COCG (field type) runs
+ * to 1e-2 of it until the FP64 residual is below tol.  FP32 arithmetic alone
+ * cannot reach tol = 1e-4 on finely graded grids: S magnifies the rounding of
+ * x by the ratio of its curl-curl and diagonal parts. */
+typedef enum { MOR_SOLVER_AUTO = 0, MOR_SOLVER_CGS = 1, MOR_SOLVER_BICGSTAB = 2, MOR_SOLVER_COCG = 3 } mor_solver;
 
 typedef struct {
   int q;              /* requested columns of V1 and of V2 (Sec. II-C "N~")        */
@@ -309,6 +317,21 @@ typedef struct {
   mor_orth orth;
   mor_solver solver;
 } mor_opts;
+
+/* A4 -- the shifted Schur-complement solves of Sec. IV-B on their own: for
+ * each of nb (<= 16) points z_b (host [nb][2], re/im) solve
+ * S(z_b) x_b = b_b, S the operator of mor_schur_apply at time step
+ * opts->dt0, to a relative residual |b - S x| / |b| <= opts->tol, with
+ * opts->solver (AUTO: CGS for FDTD_F64 grids, COCG with FP64 refinement for
+ * FDTD_F32 grids) and at most opts->maxit iterations per right-hand side.
+ * b, x: device [nb][3][nc] complex of the grid's type (x is overwritten).
+ * iters, resid: host [nb] or NULL -- iterations and final relative residual
+ * per right-hand side (for COCG the FP64 residual of the FP64 solution,
+ * before x is rounded to the grid's type).  Returns FDTD_ENOCONV when a
+ * right-hand side missed tol (x still written).  Allocates its work
+ * vectors; synchronises the stream. */
+FDTD_API fdtd_status mor_shifted_solve(fdtd_grid *grid, const mor_opts *opts, int nb, const double *z,
+                                       const void *b, void *x, int *iters, double *resid, fdtd_stream_t stream);
 
 /* Fill *opts with M = 1.1, L = 2, tol = 1e-4, maxit = 20000, defl_tol = 1e-8
  * (FP64) -- q, fmax and dt0 must still be set by the caller. */

@@ -12,8 +12,10 @@
 // Row scaling leaves the Krylov subspaces of A^{-1}(R+F) unchanged.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <complex>
 #include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "grid_internal.cuh"
@@ -106,9 +108,22 @@ struct OpArgs {
   Geo<T> g;
   const T *eps, *sig, *mu, *sgm;   // per-edge properties (3 x nc each)
   T inv_dt;
+  T vscale;                        // 1 / (volume of cell 0): edge volumes in units of it
   cplx<T> z[kMaxRhs];              // expansion point of each right-hand side
   cplx<T> cz[kMaxRhs];             // coefficient of the curl term
 };
+
+// Volume of E edge c at cell (i, j, k) -- primal length times dual area --
+// in units of the volume of cell 0; 0 on wall edges (dual length 0).
+template <typename T>
+__device__ __forceinline__ T edge_volume(const OpArgs<T> &a, int c, int i, int j, int k) {
+  const Geo<T> &g = a.g;
+  T d;
+  if (c == 0) d = g.rd(0, i) * g.rdd(1, j) * g.rdd(2, k);
+  else if (c == 1) d = g.rd(1, j) * g.rdd(0, i) * g.rdd(2, k);
+  else d = g.rd(2, k) * g.rdd(0, i) * g.rdd(1, j);
+  return d != T(0) ? a.vscale / d : T(0);
+}
 
 // r1 = (eps/dt + sig/2) v1, r2 = curlE(v1) + (mu/dt + sgm/2) v2   [(R+F) v]
 template <typename T>
@@ -139,9 +154,10 @@ template <typename T>
 __global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int64_t xstride,
                                 const cplx<T> *__restrict__ P, int64_t pstride,
                                 const cplx<T> *__restrict__ r2, int64_t r2stride,
-                                cplx<T> *__restrict__ t, int64_t tstride, const int *__restrict__ active) {
+                                cplx<T> *__restrict__ t, int64_t tstride, const int *__restrict__ active,
+                                int astride = 1) {
   const int b = blockIdx.y;
-  if (active && !active[b]) return;
+  if (active && !active[b * astride]) return;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nc = a.g.nc;
   if (n >= nc) return;
@@ -169,13 +185,17 @@ __global__ void h_from_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ x, int6
 }
 
 // Per right-hand-side scalars of the Krylov solvers (device resident).
+// itol / imaxit: per right-hand-side tolerance and iteration cap, used when
+// the scalar kernel is launched with tol <= 0 (the COCG inner solves of the
+// refinement loop, whose captured graph is replayed with changing limits).
 struct CgsScal {
   double rho_re, rho_im, alpha_re, alpha_im, beta_re, beta_im, omega_re, omega_im, rn2, bn2;
-  int active, iters, status, restarts;
+  double itol;
+  int active, iters, status, restarts, imaxit, pad;
 };
 
-enum EMode { EM_RHS = 0, EM_APPLY = 1, EM_APPLY_DOT = 2, EM_APPLY_RUPDATE = 3, EM_RESID = 4 };
-enum ScalMode { SM_INIT = 0, SM_ALPHA = 1, SM_CGS_RHO = 2, SM_OMEGA = 3, SM_BICG_RHO = 4, SM_VERIFY = 5 };
+enum EMode { EM_RHS = 0, EM_APPLY = 1, EM_APPLY_DOT = 2, EM_APPLY_RUPDATE = 3, EM_RESID = 4, EM_APPLY_VDOT = 5 };
+enum ScalMode { SM_INIT = 0, SM_ALPHA = 1, SM_CGS_RHO = 2, SM_OMEGA = 3, SM_BICG_RHO = 4, SM_VERIFY = 5, SM_NORM = 6 };
 
 // Sums nv (<= 3) doubles over the block (blockDim.x a multiple of 32, <= 1024);
 // the totals are valid in vals[] of thread 0.  sh holds >= 3*32 doubles.
@@ -196,8 +216,104 @@ __device__ __forceinline__ void block_sum(double *vals, int nv, double *sh) {
   }
 }
 
+// Update of one right-hand side's scalars from its summed partials acc.
+__device__ void scal_update(CgsScal &s, const double *acc, int mode, double tol, int maxit, int max_restarts) {
+  if (tol <= 0) { tol = s.itol; maxit = s.imaxit; }
+  const cplx<double> rho(s.rho_re, s.rho_im), d(acc[0], acc[1]);
+  auto breakdown = [&]() { s.status = 2; s.active = 0; };
+  if (mode == SM_NORM) {
+    s.rn2 = acc[2];
+  } else if (mode == SM_INIT) {
+    s.rho_re = acc[0]; s.rho_im = acc[1]; s.rn2 = acc[2]; s.bn2 = acc[2];
+    s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
+    s.iters = 0; s.status = 0; s.restarts = 0;
+    s.active = acc[2] > 0 ? 1 : 0;   // zero right-hand side: x = 0
+  } else if (mode == SM_ALPHA) {
+    const double ad = sqrt(norm2(d));
+    if (ad == 0 || !isfinite(ad)) breakdown();
+    else { const cplx<double> al = cdiv(rho, d); s.alpha_re = al.re; s.alpha_im = al.im; }
+  } else if (mode == SM_OMEGA) {
+    if (!(acc[2] > 0) || !isfinite(acc[2])) breakdown();
+    else { s.omega_re = acc[0] / acc[2]; s.omega_im = -acc[1] / acc[2]; }
+    if (s.omega_re == 0 && s.omega_im == 0) breakdown();
+  } else if (mode == SM_CGS_RHO || mode == SM_BICG_RHO) {
+    s.rn2 = acc[2];
+    s.iters += 1;
+    if (!isfinite(acc[2]) || acc[2] > 1e16 * s.bn2) breakdown();   // diverged
+    else if (sqrt(acc[2]) <= tol * sqrt(s.bn2)) s.active = 0;
+    else if (s.iters >= maxit) { s.status = 1; s.active = 0; }
+    else if (norm2(rho) == 0) breakdown();
+    else {
+      cplx<double> be = cdiv(d, rho);
+      if (mode == SM_BICG_RHO) be = be * cdiv(cplx<double>(s.alpha_re, s.alpha_im), cplx<double>(s.omega_re, s.omega_im));
+      s.beta_re = be.re; s.beta_im = be.im;
+      s.rho_re = d.re; s.rho_im = d.im;
+    }
+  } else {  // SM_VERIFY: acc[2] = |b - S x|^2
+    s.rn2 = acc[2];
+    const bool ok = isfinite(acc[2]) && sqrt(acc[2]) <= 2.0 * tol * sqrt(s.bn2);
+    if (!ok && s.restarts < max_restarts && s.iters < maxit) {
+      s.restarts += 1; s.active = 1; s.status = 0;
+      s.rho_re = acc[2]; s.rho_im = 0; s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
+    } else if (!ok && s.status == 0) {
+      s.status = 3;  // true residual above tolerance after the last restart
+    }
+  }
+}
+
+__global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict__ partials, CgsScal *sc,
+                                      int mode, double tol, int maxit, int max_restarts) {
+  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (b >= nb) return;
+  if (mode != SM_VERIFY && mode != SM_INIT && mode != SM_NORM && !sc[b].active) return;  // uniform across the warp
+  if (mode == SM_VERIFY && sc[b].status == 1) return;                  // iteration cap reached
+  double acc[3] = {0, 0, 0};
+#pragma unroll 8
+  for (int blk = lane; blk < nblk; blk += 32) {  // unrolled: the loads go out together
+    const double *p = partials + ((size_t)b * nblk + blk) * 3;
+    acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
+  }
+  for (int o = 16; o; o >>= 1) {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+  }
+  if (lane == 0) scal_update(sc[b], acc, mode, tol, maxit, max_restarts);
+}
+
+// Scalar update fused into a producing kernel: each CTA has stored its
+// partial triple for right-hand side b; the CTA that takes the last ticket
+// sums all gridDim.x triples of b (fixed order: thread-strided, then the
+// block tree), applies `mode` with the per-RHS limits and returns the ticket
+// counter to 0 for the next launch.  No CTA waits for another.
+__device__ void last_block_scalars(int b, const double *partials, unsigned *tickets, CgsScal *sc, int mode,
+                                   double *sh, int nparts = -1) {
+  __shared__ int last;
+  if (nparts < 0) nparts = (int)gridDim.x;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&tickets[b], 1u) == (unsigned)nparts - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[3] = {0, 0, 0};
+  const double *pb = partials + (size_t)b * nparts * 3;
+  for (int blk = threadIdx.x; blk < nparts; blk += blockDim.x) {
+    acc[0] += __ldcg(pb + 3 * blk);
+    acc[1] += __ldcg(pb + 3 * blk + 1);
+    acc[2] += __ldcg(pb + 3 * blk + 2);
+  }
+  block_sum(acc, 3, sh);
+  if (threadIdx.x == 0) {
+    scal_update(sc[b], acc, mode, -1.0, 0, 0);
+    tickets[b] = 0;
+  }
+}
+
 // y = A + cz curlH(t), A = r1 (EM_RHS) or a11(z) P x (apply modes); dead E edges 0.
-// EM_APPLY_DOT: partials of rt^H y and |y|^2.  EM_APPLY_RUPDATE: r -= alpha y,
+// EM_APPLY_DOT: partials of rt^H y and |y|^2.  EM_APPLY_VDOT: partials of the
+// unconjugated volume-weighted product sum_e V_e x_e y_e (COCG's (p, S p)_V).
+// EM_APPLY_RUPDATE: r -= alpha y,
 // partials of rt^H r and |r|^2 (y not stored).  EM_RESID: true residual
 // y = bhat - S x (bhat passed in rt), partials of |y|^2.
 template <typename T, int MODE>
@@ -206,7 +322,8 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
                                 const cplx<T> *__restrict__ P, int64_t pstride,
                                 cplx<T> *__restrict__ y, int64_t ystride,
                                 const cplx<T> *__restrict__ rt, cplx<T> *__restrict__ r, int64_t rstride,
-                                const CgsScal *__restrict__ sc, double *__restrict__ partials) {
+                                const CgsScal *__restrict__ sc, double *__restrict__ partials,
+                                unsigned *__restrict__ tickets = nullptr) {
   __shared__ double sh[3 * 32];
   const int b = blockIdx.y;
   if (sc && MODE != EM_RESID && !sc[b].active) return;
@@ -240,7 +357,15 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
         }
         out = A + a.cz[b] * ch[c];
       }
-      if (MODE == EM_APPLY_DOT) {
+      if (MODE == EM_APPLY_VDOT) {
+        if (ep != T(0)) {
+          const cplx<T> w = edge_volume(a, c, i, j, k) * (x[b * xstride + e] * out);
+          s0 += w.re;
+          s1 += w.im;
+        }
+        s2 += norm2(out);
+        y[b * ystride + e] = out;
+      } else if (MODE == EM_APPLY_DOT) {
         const cplx<T> w = conj(rt[b * rstride + e]) * out;
         s0 += w.re;
         s1 += w.im;
@@ -268,13 +393,146 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
     acc[1] = (double)s1;
     acc[2] = (double)s2;
   }
-  if (MODE == EM_APPLY_DOT || MODE == EM_APPLY_RUPDATE || MODE == EM_RESID) {
+  if (MODE == EM_APPLY_DOT || MODE == EM_APPLY_VDOT || MODE == EM_APPLY_RUPDATE || MODE == EM_RESID) {
     block_sum(acc, 3, sh);
     if (threadIdx.x == 0) {
       double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
       pb[0] = acc[0]; pb[1] = acc[1]; pb[2] = acc[2];
     }
+    // COCG: alpha = rho / (p, S p)_V by the last CTA of this right-hand side
+    if (MODE == EM_APPLY_VDOT && tickets) last_block_scalars(b, partials, tickets, const_cast<CgsScal *>(sc), SM_ALPHA, sh);
   }
+}
+
+// ------------------------------------------- fused one-pass Schur apply
+// q = a11 p + z curlH(curlE(p) / a22) in one pass over memory: the H-part
+// intermediate t lives in shared memory only.  A CTA owns a tile of
+// kSX x kSY cells in x, y and marches a chunk of z planes upwards.  Per plane
+// k: warps 0..kSY compute t(k) = curlE(p)/a22 on rows j0-1 .. j0+kSY-1 of the
+// tile's 32 columns and warp kSY+1 on the -x halo column (i0-1), into the
+// plane-parity slot of the shared tile; after one barrier warps 1..kSY form q
+// at their own cells from t(k) (own, -x, -y neighbours) and t(k-1) (own
+// position, kept in registers).  Two parity slots make one barrier per plane
+// enough.  H edges outside the grid contribute zero, as in curl_h3.
+// VDOT: partials of (p, q)_V and, with tickets, alpha = rho / (p, q)_V by
+// the last CTA of each right-hand side.  Grid: (nb, tiles, z chunks).
+constexpr int kSX = 32, kSY = 8;
+constexpr int kSThreads = 32 * (kSY + 2);
+
+template <typename T, bool VDOT>
+__global__ void __launch_bounds__(kSThreads) schur_fused_kernel(OpArgs<T> a, const cplx<T> *__restrict__ p,
+                                                                cplx<T> *__restrict__ q, int64_t stride, int ntx,
+                                                                int zchunk, CgsScal *__restrict__ sc,
+                                                                double *__restrict__ partials,
+                                                                unsigned *__restrict__ tickets) {
+  __shared__ cplx<T> ts[2][3][kSY + 1][kSX + 1];
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.x;
+  if (VDOT && sc && !sc[b].active) return;
+  const Geo<T> &g = a.g;
+  const int64_t nc = g.nc, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  const int tile = blockIdx.y, i0 = (tile % ntx) * kSX, j0 = (tile / ntx) * kSY;
+  const int k0 = blockIdx.z * zchunk, k1 = min(g.nz, k0 + zchunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // phase-1 position of this thread
+  int pi, pj, prow, pcol;
+  if (warp <= kSY) { pi = i0 + lane; pj = j0 - 1 + warp; prow = warp; pcol = lane + 1; }
+  else { pi = i0 - 1; pj = j0 - 1 + lane; prow = lane; pcol = 0; }
+  const bool p1 = (warp <= kSY || lane <= kSY) && pi >= 0 && pi < g.nx && pj >= 0 && pj < g.ny;
+  const bool own = warp >= 1 && warp <= kSY && pi < g.nx && pj < g.ny;  // phase-2 owner (i = pi, j = pj)
+  const cplx<T> *pb = p + b * stride;
+  const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+  // t = curlE(p) / a22 at H edges of cell (i, j, kk); pe* return own E at kk
+  auto tcomp = [&](int i, int j, int kk, cplx<T> out[3], cplx<T> own_e[3]) {
+    const int64_t n = g.id(i, j, kk);
+    auto ld = [&](int64_t idx) { return pb[idx]; };
+    cplx<T> ce[3];
+    curl_e3<T, cplx<T>>(g, ld, i, j, kk, n, ce);
+    own_e[0] = pb[n]; own_e[1] = pb[nc + n]; own_e[2] = pb[2 * nc + n];
+    for (int c = 0; c < 3; ++c) {
+      const int64_t e = c * nc + n;
+      const T mu = a.mu[e];
+      cplx<T> o;
+      if (mu != T(0)) {
+        const cplx<T> a22 = (mu * a.inv_dt) * zm1 + (T(0.5) * a.sgm[e]) * zp1;
+        o = cdiv(ce[c], a22);
+      }
+      out[c] = o;
+    }
+  };
+  cplx<T> tprev[3], pe[3], tk[3];
+  if (own && k0 > 0) tcomp(pi, pj, k0 - 1, tprev, pe);
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int kk = k0; kk < k1; ++kk) {
+    const int par = kk & 1;
+    if (p1) {
+      tcomp(pi, pj, kk, tk, pe);
+    } else {
+      tk[0] = tk[1] = tk[2] = cplx<T>();
+    }
+    if (warp <= kSY || lane <= kSY)
+      for (int c = 0; c < 3; ++c) ts[par][c][prow][pcol] = tk[c];
+    __syncthreads();
+    if (own) {
+      const int i = pi, j = pj, r = prow, cl = pcol;
+      const int64_t n = g.id(i, j, kk);
+      const cplx<T> hx = ts[par][0][r][cl], hy = ts[par][1][r][cl], hz = ts[par][2][r][cl];
+      const cplx<T> hz_jm = ts[par][2][r - 1][cl], hx_jm = ts[par][0][r - 1][cl];
+      const cplx<T> hz_im = ts[par][2][r][cl - 1], hy_im = ts[par][1][r][cl - 1];
+      const cplx<T> hy_km = kk > 0 ? tprev[1] : cplx<T>(), hx_km = kk > 0 ? tprev[0] : cplx<T>();
+      const T rx = g.rdd(0, i), ry = g.rdd(1, j), rz = g.rdd(2, kk);
+      cplx<T> ch[3];
+      ch[0] = ry * (hz - hz_jm) - rz * (hy - hy_km);
+      ch[1] = rz * (hx - hx_km) - rx * (hz - hz_im);
+      ch[2] = rx * (hy - hy_im) - ry * (hx - hx_jm);
+      for (int c = 0; c < 3; ++c) {
+        const int64_t e = c * nc + n;
+        const T ep = a.eps[e];
+        cplx<T> out;
+        if (ep != T(0)) {
+          const cplx<T> a11 = (ep * a.inv_dt) * zm1 + (T(0.5) * a.sig[e]) * zp1;
+          out = a11 * pe[c] + a.cz[b] * ch[c];
+          if (VDOT) {
+            const cplx<T> w = edge_volume(a, c, i, j, kk) * (pe[c] * out);
+            s0 += w.re;
+            s1 += w.im;
+          }
+          s2 += norm2(out);
+        }
+        q[b * stride + e] = out;
+      }
+      tprev[0] = tk[0]; tprev[1] = tk[1]; tprev[2] = tk[2];
+    }
+  }
+  (void)sy; (void)sz;
+  if (VDOT) {
+    double acc[3] = {(double)s0, (double)s1, (double)s2};
+    block_sum(acc, 3, sh);
+    const int nparts = gridDim.y * gridDim.z;
+    const int part = blockIdx.y + gridDim.y * blockIdx.z;
+    if (threadIdx.x == 0) {
+      double *pp = partials + ((size_t)b * nparts + part) * 3;
+      pp[0] = acc[0]; pp[1] = acc[1]; pp[2] = acc[2];
+    }
+    if (tickets) last_block_scalars(b, partials, tickets, sc, SM_ALPHA, sh, nparts);
+  }
+}
+
+// Launch shape of schur_fused_kernel: tiles of kSX x kSY and z chunks sized
+// for about four CTAs per SM over all right-hand sides.
+struct SchurShape {
+  int ntx, nty, zchunk, nchunk;
+};
+inline SchurShape schur_shape(const fdtd_grid *g, int nb) {
+  SchurShape sh;
+  sh.ntx = (g->nx + kSX - 1) / kSX;
+  sh.nty = (g->ny + kSY - 1) / kSY;
+  const int64_t per = (int64_t)sh.ntx * sh.nty * nb;
+  int want = (int)std::max<int64_t>(1, (152 * 4 + per - 1) / per);
+  want = std::min(want, std::max(1, g->nz / 4));
+  sh.zchunk = (g->nz + want - 1) / want;
+  sh.nchunk = (g->nz + sh.zchunk - 1) / sh.zchunk;
+  return sh;
 }
 
 // Jacobi preconditioner: P = 1 / diag(S(z)) on live E edges, 0 on dead ones.
@@ -314,6 +572,260 @@ __global__ void jacobi_kernel(OpArgs<T> a, cplx<T> *__restrict__ P, int64_t pstr
       out = cdiv(cplx<T>(T(1)), a11 + a.z[b] * sum);
     }
     P[b * pstride + e] = out;
+  }
+}
+
+// ------------------------------------------------- COCG with a gradient-space
+// correction of the Jacobi preconditioner.  The Schur complement
+// S = A11 - A12 A22^{-1} A21 of A(z) = z(R+F) - (R-F) is complex symmetric
+// (A11, A22 diagonal, A21 = -z A12^T); in the per-volume rows used here it is
+// self-adjoint in the unconjugated form (u, w)_V = sum_e V_e u_e w_e, so the
+// conjugate-orthogonal CG applies with that product.  Gradient fields G phi
+// (G the discrete gradient from grid nodes to E edges, curlE G = 0) are
+// annihilated by the curl-curl part, so S G phi = a11 G phi: near z = 1 these
+// are the near-null directions a diagonal preconditioner leaves to the Krylov
+// method.  The preconditioner adds one damped Jacobi step on the nodal
+// operator N = G^T diag(V a11) G:
+//   P w = w / diag(S) + G (omega (G^T V w) / diag(N)),
+// with phi = 0 on wall nodes and on nodes touching a dead (PEC) edge.  P is
+// symmetric in the same product, as COCG requires.
+constexpr double kNodalOmega = 0.8;
+
+// diag(N) per node and right-hand side; 0 marks nodes held at phi = 0.
+// Node (i, j, k) is the lower corner of cell (i, j, k); its six E edges are
+// Ex(i-1|i, j, k), Ey(i, j-1|j, k), Ez(i, j, k-1|k).  For both x edges of a
+// node rd_e V_e equals the dual area 1/(rdd_y rdd_z), likewise for y and z.
+template <typename T>
+__global__ void cocg_dn_kernel(OpArgs<T> a, cplx<T> *__restrict__ dN) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+  const Geo<T> &g = a.g;
+  cplx<T> out;
+  if (i >= 1 && j >= 1 && k >= 1) {  // i < nx etc. by construction; the far walls are not stored
+    const int64_t sx = 1, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const int64_t lo[3] = {n - sx, n - sy, n - sz};
+    const int idx[3] = {i, j, k};
+    const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
+    bool live = true;
+    cplx<T> acc;
+    for (int c = 0; c < 3 && live; ++c) {
+      const T area = c == 0 ? T(1) / (g.rdd(1, j) * g.rdd(2, k))
+                   : (c == 1 ? T(1) / (g.rdd(0, i) * g.rdd(2, k)) : T(1) / (g.rdd(0, i) * g.rdd(1, j)));
+      for (int h = 0; h < 2; ++h) {
+        const int64_t e = c * nc + (h ? n : lo[c]);
+        const T ep = a.eps[e];
+        if (ep == T(0)) { live = false; break; }
+        const cplx<T> a11 = (ep * a.inv_dt) * zm1 + (T(0.5) * a.sig[e]) * zp1;
+        acc = acc + (a.vscale * area * g.rd(c, idx[c] - 1 + h)) * a11;
+      }
+    }
+    if (live) out = acc;
+  }
+  dN[b * nc + n] = out;
+}
+
+// phi = omega (G^T V (r - alpha q)) / diag(N) per node (INIT: alpha = 0, q unused).
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(MB) cocg_node_kernel(OpArgs<T> a, const cplx<T> *__restrict__ r,
+                                                       const cplx<T> *__restrict__ q, int64_t stride,
+                                                       const cplx<T> *__restrict__ dN, cplx<T> *__restrict__ phi,
+                                                       const CgsScal *__restrict__ sc) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  const cplx<T> dn = dN[b * nc + n];
+  cplx<T> out;
+  if (dn.re != T(0) || dn.im != T(0)) {  // live node: interior, all six edges live
+    int i, j, k;
+    cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+    const Geo<T> &g = a.g;
+    cplx<T> alpha;
+    if (!INIT) alpha = cplx<T>((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+    const cplx<T> *rb = r + b * stride;
+    const cplx<T> *qb = INIT ? nullptr : q + b * stride;
+    auto w = [&](int64_t e) { return INIT ? rb[e] : rb[e] - alpha * qb[e]; };
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const cplx<T> fx = w(n - 1) - w(n), fy = w(nc + n - sy) - w(nc + n), fz = w(2 * nc + n - sz) - w(2 * nc + n);
+    const T ax = T(1) / (g.rdd(1, j) * g.rdd(2, k)), ay = T(1) / (g.rdd(0, i) * g.rdd(2, k)),
+            az = T(1) / (g.rdd(0, i) * g.rdd(1, j));
+    const cplx<T> f = (a.vscale * ax) * fx + (a.vscale * ay) * fy + (a.vscale * az) * fz;
+    out = (T)kNodalOmega * cdiv(f, dn);
+  }
+  phi[b * nc + n] = out;
+}
+
+// Edge pass of a COCG iteration: r' = r - alpha q, x += alpha p,
+// zv = P r' = r' / diag(S) + G phi; partials (r', zv)_V and |r'|^2.
+// INIT: r' = r, x untouched, partials written for every right-hand side
+// (zero for inactive ones, which SM_INIT then leaves inactive).
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(MB) cocg_edge_kernel(OpArgs<T> a, cplx<T> *__restrict__ r,
+                                                       const cplx<T> *__restrict__ q, cplx<T> *__restrict__ x,
+                                                       const cplx<T> *__restrict__ p, const cplx<T> *__restrict__ phi,
+                                                       const cplx<T> *__restrict__ Jinv, cplx<T> *__restrict__ zv,
+                                                       int64_t stride, CgsScal *__restrict__ sc,
+                                                       double *__restrict__ partials, unsigned *__restrict__ tickets) {
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.y;
+  const bool active = sc[b].active != 0;
+  if (!active && !INIT) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  double acc[3] = {0, 0, 0};
+  if (active && n < nc) {
+    int i, j, k;
+    cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+    const Geo<T> &g = a.g;
+    cplx<T> alpha;
+    if (!INIT) alpha = cplx<T>((T)sc[b].alpha_re, (T)sc[b].alpha_im);
+    const cplx<T> *phb = phi + b * nc;
+    const cplx<T> ph0 = phb[n];
+    const int idx[3] = {i, j, k}, nax[3] = {g.nx, g.ny, g.nz};
+    const int64_t st[3] = {1, g.nx, (int64_t)g.nx * g.ny};
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      const int64_t e = c * nc + n, o = b * stride + e;
+      if (a.eps[e] == T(0)) {
+        if (!INIT) r[o] = cplx<T>();
+        zv[o] = cplx<T>();
+        continue;
+      }
+      cplx<T> rv = r[o];
+      if (!INIT) {
+        rv = rv - alpha * q[o];
+        r[o] = rv;
+        x[o] = x[o] + alpha * p[o];
+      }
+      const cplx<T> ph1 = idx[c] + 1 < nax[c] ? phb[n + st[c]] : cplx<T>();
+      const cplx<T> zz = Jinv[o] * rv + g.rd(c, idx[c]) * (ph1 - ph0);
+      zv[o] = zz;
+      const cplx<T> wv = edge_volume(a, c, i, j, k) * (rv * zz);
+      s0 += wv.re;
+      s1 += wv.im;
+      s2 += norm2(rv);
+    }
+    acc[0] = (double)s0;
+    acc[1] = (double)s1;
+    acc[2] = (double)s2;
+  }
+  block_sum(acc, 3, sh);
+  if (threadIdx.x == 0) {
+    double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+    pb[0] = acc[0]; pb[1] = acc[1]; pb[2] = acc[2];
+  }
+  // convergence test and beta = rho'/rho by the last CTA of this right-hand side
+  if (!INIT && tickets) last_block_scalars(b, partials, tickets, sc, SM_CGS_RHO, sh);
+}
+
+// COCG: p = zv + beta p
+template <typename T>
+__global__ void cocg_update_p_kernel(int64_t len, const CgsScal *__restrict__ sc, const cplx<T> *__restrict__ zv,
+                                     cplx<T> *__restrict__ p, int64_t stride) {
+  const int b = blockIdx.y;
+  if (!sc[b].active) return;
+  const cplx<T> beta((T)sc[b].beta_re, (T)sc[b].beta_im);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    p[o] = zv[o] + beta * p[o];
+  }
+}
+
+// Refinement loop, FP64 residual r = bhat - S x of the FP64 solution x (the
+// FP32 iterates lose the near-static gradient part of x to rounding: S
+// amplifies a relative error eps of x by the ratio of its curl-curl and
+// diagonal parts, about 1e4 on finely graded cells).  Material properties and
+// axis tables are those of the grid, converted to double.
+template <typename T>
+__global__ void __launch_bounds__(MB) resid64_h_kernel(OpArgs<T> a, const cplx<double> *__restrict__ x,
+                                                       cplx<double> *__restrict__ t, int64_t stride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+  const cplx<double> *xb = x + b * stride;
+  auto ld = [&](int64_t idx) { return xb[idx]; };
+  const cplx<double> z((double)a.z[b].re, (double)a.z[b].im), zm1(z.re - 1.0, z.im), zp1(z.re + 1.0, z.im);
+  cplx<double> ce[3];
+  curl_e3<T, cplx<double>>(a.g, ld, i, j, k, n, ce);
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const double mu = (double)a.mu[e];
+    cplx<double> out;
+    if (mu != 0.0) {
+      const cplx<double> a22 = (mu * (double)a.inv_dt) * zm1 + (0.5 * (double)a.sgm[e]) * zp1;
+      out = cdiv(ce[c], a22);
+    }
+    t[b * stride + e] = out;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MB) resid64_e_kernel(OpArgs<T> a, const cplx<double> *__restrict__ t,
+                                                       const cplx<double> *__restrict__ x, int64_t stride,
+                                                       const cplx<T> *__restrict__ bhat, cplx<T> *__restrict__ rout,
+                                                       double *__restrict__ partials) {
+  __shared__ double sh[3 * 32];
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  double acc[3] = {0, 0, 0};
+  if (n < nc) {
+    int i, j, k;
+    cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+    const cplx<double> *tb = t + b * stride;
+    auto ld = [&](int64_t idx) { return tb[idx]; };
+    const cplx<double> z((double)a.z[b].re, (double)a.z[b].im), zm1(z.re - 1.0, z.im), zp1(z.re + 1.0, z.im);
+    cplx<double> ch[3];
+    curl_h3<T, cplx<double>>(a.g, ld, i, j, k, n, ch);
+    for (int c = 0; c < 3; ++c) {
+      const int64_t e = c * nc + n, o = b * stride + e;
+      const double ep = (double)a.eps[e];
+      cplx<double> rv;
+      if (ep != 0.0) {
+        const cplx<double> a11 = (ep * (double)a.inv_dt) * zm1 + (0.5 * (double)a.sig[e]) * zp1;
+        const cplx<T> bh = bhat[o];
+        rv = cplx<double>((double)bh.re, (double)bh.im) - (a11 * x[o] + z * ch[c]);
+      }
+      rout[o] = cplx<T>((T)rv.re, (T)rv.im);
+      acc[2] += norm2(rv);
+    }
+  }
+  block_sum(acc, 3, sh);
+  if (threadIdx.x == 0) {
+    double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+    pb[0] = 0; pb[1] = 0; pb[2] = acc[2];
+  }
+}
+
+// x64 += d for the right-hand sides of the last inner solve (flag per RHS)
+template <typename T>
+__global__ void acc64_kernel(int64_t len, const int *__restrict__ upd, const cplx<T> *__restrict__ d,
+                             cplx<double> *__restrict__ x, int64_t stride) {
+  const int b = blockIdx.y;
+  if (!upd[b]) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b * stride + e;
+    const cplx<T> v = d[o];
+    x[o] = x[o] + cplx<double>((double)v.re, (double)v.im);
+  }
+}
+
+// out[b] (stride ostride) = x64[b] in the field type
+template <typename T>
+__global__ void from64_kernel(int64_t len, const cplx<double> *__restrict__ x, int64_t stride,
+                              cplx<T> *__restrict__ out, int64_t ostride) {
+  const int b = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const cplx<double> v = x[b * stride + e];
+    out[b * ostride + e] = cplx<T>((T)v.re, (T)v.im);
   }
 }
 
@@ -360,70 +872,12 @@ __global__ void cgs_update2_kernel(int64_t len, const CgsScal *__restrict__ sc, 
 //   SM_OMEGA:    omega = (t^H s)/(t^H t) from s^H t and |t|^2              (BiCGSTAB)
 //   SM_BICG_RHO: rho' = rt^H r, |r|^2 -> convergence; beta = (rho'/rho)(alpha/omega)
 //   SM_VERIFY:   true residual |b - S x|^2: restart (rt = r) when above tolerance
+//   SM_NORM:     |r|^2 into rn2 only (every right-hand side)
+// COCG reuses SM_INIT (rho = (r, P r)_V), SM_ALPHA (alpha = rho / (p, S p)_V)
+// and SM_CGS_RHO (rho' = (r, P r)_V, beta = rho'/rho).
 // One warp per right-hand side (launch with 32 * nb threads): the warp sums
 // that right-hand side's nblk partial triples in a fixed order (lane-strided,
 // then a shuffle tree), and lane 0 updates its scalars.
-__global__ void solver_scalars_kernel(int nb, int nblk, const double *__restrict__ partials, CgsScal *sc,
-                                      int mode, double tol, int maxit, int max_restarts) {
-  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (b >= nb) return;
-  {
-    if (mode != SM_VERIFY && mode != SM_INIT && !sc[b].active) return;  // uniform across the warp
-    if (mode == SM_VERIFY && sc[b].status == 1) return;                  // iteration cap reached
-    double acc[3] = {0, 0, 0};
-#pragma unroll 8
-    for (int blk = lane; blk < nblk; blk += 32) {  // unrolled: the loads go out together
-      const double *p = partials + ((size_t)b * nblk + blk) * 3;
-      acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
-    }
-    for (int o = 16; o; o >>= 1) {
-      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
-      acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
-      acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
-    }
-    if (lane == 0) {
-      CgsScal &s = sc[b];
-      const cplx<double> rho(s.rho_re, s.rho_im), d(acc[0], acc[1]);
-      auto breakdown = [&]() { s.status = 2; s.active = 0; };
-      if (mode == SM_INIT) {
-        s.rho_re = acc[0]; s.rho_im = 0; s.rn2 = acc[2]; s.bn2 = acc[2];
-        s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
-        s.iters = 0; s.status = 0; s.restarts = 0;
-        s.active = acc[2] > 0 ? 1 : 0;   // zero right-hand side: x = 0
-      } else if (mode == SM_ALPHA) {
-        const double ad = sqrt(norm2(d));
-        if (ad == 0 || !isfinite(ad)) breakdown();
-        else { const cplx<double> al = cdiv(rho, d); s.alpha_re = al.re; s.alpha_im = al.im; }
-      } else if (mode == SM_OMEGA) {
-        if (!(acc[2] > 0) || !isfinite(acc[2])) breakdown();
-        else { s.omega_re = acc[0] / acc[2]; s.omega_im = -acc[1] / acc[2]; }
-        if (s.omega_re == 0 && s.omega_im == 0) breakdown();
-      } else if (mode == SM_CGS_RHO || mode == SM_BICG_RHO) {
-        s.rn2 = acc[2];
-        s.iters += 1;
-        if (!isfinite(acc[2]) || acc[2] > 1e16 * s.bn2) breakdown();   // diverged
-        else if (sqrt(acc[2]) <= tol * sqrt(s.bn2)) s.active = 0;
-        else if (s.iters >= maxit) { s.status = 1; s.active = 0; }
-        else if (norm2(rho) == 0) breakdown();
-        else {
-          cplx<double> be = cdiv(d, rho);
-          if (mode == SM_BICG_RHO) be = be * cdiv(cplx<double>(s.alpha_re, s.alpha_im), cplx<double>(s.omega_re, s.omega_im));
-          s.beta_re = be.re; s.beta_im = be.im;
-          s.rho_re = d.re; s.rho_im = d.im;
-        }
-      } else {  // SM_VERIFY: acc[2] = |b - S x|^2
-        s.rn2 = acc[2];
-        const bool ok = isfinite(acc[2]) && sqrt(acc[2]) <= 2.0 * tol * sqrt(s.bn2);
-        if (!ok && s.restarts < max_restarts && s.iters < maxit) {
-          s.restarts += 1; s.active = 1; s.status = 0;
-          s.rho_re = acc[2]; s.rho_im = 0; s.beta_re = s.beta_im = 0; s.omega_re = 1; s.omega_im = 0;
-        } else if (!ok && s.status == 0) {
-          s.status = 3;  // true residual above tolerance after the last restart
-        }
-      }
-    }
-  }
-}
 
 // Restart of the active right-hand sides: shadow residual rt = r, search
 // directions zero.
@@ -639,6 +1093,10 @@ struct Work {
   DevBuf sc;       // nb CgsScal
   DevBuf dots;     // kMaxDots*2 doubles
   DevBuf dpart;    // 2*kMaxDots x nblk_dot doubles
+  DevBuf x64, t64; // nb x 3nc complex FP64: refined solution and H-part temporary (COCG)
+  DevBuf phi, dN;  // nb x nc nodal potential and nodal diagonal (COCG)
+  DevBuf upd;      // nb ints: right-hand sides the last inner solve updated
+  DevBuf tickets;  // 2 x kMaxRhs CTA tickets of the fused scalar updates (COCG)
 };
 
 template <typename T>
@@ -652,6 +1110,7 @@ static OpArgs<T> make_op(fdtd_grid *g, double dt0, const std::vector<std::comple
   a.mu = ep + EP_MU * 3 * g->nc;
   a.sgm = ep + EP_SGM * 3 * g->nc;
   a.inv_dt = (T)(1.0 / dt0);
+  a.vscale = (T)(1.0 / (g->dx[0] * g->dy[0] * g->dz[0]));
   for (size_t b = 0; b < zs.size(); ++b) {
     a.z[b] = cplx<T>((T)zs[b].real(), (T)zs[b].imag());
     a.cz[b] = cplx<T>((T)czs[b].real(), (T)czs[b].imag());
@@ -699,59 +1158,271 @@ struct BasisBuilder {
   bool last_failed = false;
   int fallbacks = 0;
   std::vector<int> rhs_failed;  // per right-hand side, of the last solve
+  std::vector<int> rhs_iters;   // per right-hand side, of the last solve
+  std::vector<double> rhs_resid;
   cudaStream_t cap = nullptr;   // private stream the solver iterations are captured on
+  cudaGraphExec_t cocg_graph = nullptr;  // 16 captured COCG iterations (the buffers and points
+  int64_t cocg_graph_launches = 0;       // are fixed for a whole build)
+  int outer_max = 0;            // most refinement steps one shifted solve took (COCG)
 
   BasisBuilder(fdtd_grid *g_, const mor_opts &o_, cudaStream_t s_) : g(g_), o(o_), s(s_) {
     nc = g->nc;
     nblk = (int)((nc + MB - 1) / MB);
   }
   ~BasisBuilder() {
+    if (cocg_graph) cudaGraphExecDestroy(cocg_graph);
     if (cap) cudaStreamDestroy(cap);
   }
   BasisBuilder(const BasisBuilder &) = delete;
   BasisBuilder &operator=(const BasisBuilder &) = delete;
 
   // Solve A(z_b) x = (R+F) v for every active right-hand side b (x = [x1; x2]
-  // written to out, nb x 6nc).  v: nb x 6nc.
-  // AUTO: the paper's CGS on FP64 grids, falling back to BiCGSTAB for the whole
-  // block when a right-hand side fails; BiCGSTAB on FP32 grids.
+  // written to out, nb x 6nc).  v: nb x 6nc (B itself when from_b).
   fdtd_status solve(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
                     const cplx<T> *vin, cplx<T> *out) {
-    if (o.solver != MOR_SOLVER_AUTO) return solve_with(w, zs, from_b, vin, out, o.solver);
-    if (g->prec != FDTD_F64) return solve_with(w, zs, from_b, vin, out, MOR_SOLVER_BICGSTAB);
-    const bool nc0 = noconv;
-    const int it0 = max_iters;
-    const double r0 = max_resid;
-    FDTD_CHECK(solve_with(w, zs, from_b, vin, out, MOR_SOLVER_CGS));
-    if (!last_failed) return FDTD_OK;
-    noconv = nc0; max_iters = it0; max_resid = r0;
-    fallbacks += 1;
-    return solve_with(w, zs, from_b, vin, out, MOR_SOLVER_BICGSTAB);
+    FDTD_CHECK(make_rhs(w, zs, from_b, vin));
+    FDTD_CHECK(schur_solve(w, zs));
+    return recover(w, zs, out);
   }
 
-  fdtd_status solve_with(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
-                         const cplx<T> *vin, cplx<T> *out, int solver) {
+  // bhat = r1 + curlH(r2 / a22) of r = (R+F) v (or of r = B already in w.r)
+  fdtd_status make_rhs(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b, const cplx<T> *vin) {
     const int nb = (int)zs.size();
     const int64_t n3 = 3 * nc, n6 = 6 * nc;
-    std::vector<std::complex<double>> one(nb, 1.0), negz(nb), zz(zs);
-    for (int b = 0; b < nb; ++b) negz[b] = -zs[b];
+    std::vector<std::complex<double>> one(nb, 1.0);
     dim3 grid2(nblk, nb);
-    cplx<T> *r = w.r.template as<cplx<T>>();
+    cplx<T> *r = w.r.template as<cplx<T>>(), *t = w.t.template as<cplx<T>>();
+    OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
     if (!from_b) {
-      OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
       rpf_kernel<T><<<grid2, MB, 0, s>>>(a, vin, n6, r, n6);
       FDTD_CHECK(after_launch("rpf_kernel"));
     }
-    // b^ = r1 + curlH(r2 / a22)
-    cplx<T> *t = w.t.template as<cplx<T>>();
-    {
-      OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
-      h_from_e_kernel<T><<<grid2, MB, 0, s>>>(a, nullptr, 0, nullptr, 0, r + n3, n6, t, n3, nullptr);
-      FDTD_CHECK(after_launch("h_from_e_kernel"));
-      e_from_h_kernel<T, EM_RHS><<<grid2, MB, 0, s>>>(a, t, n3, r, n6, nullptr, 0, w.bhat.template as<cplx<T>>(), n3,
-                                                      nullptr, nullptr, 0, nullptr, nullptr);
-      FDTD_CHECK(after_launch("e_from_h_kernel"));
+    h_from_e_kernel<T><<<grid2, MB, 0, s>>>(a, nullptr, 0, nullptr, 0, r + n3, n6, t, n3, nullptr);
+    FDTD_CHECK(after_launch("h_from_e_kernel"));
+    e_from_h_kernel<T, EM_RHS><<<grid2, MB, 0, s>>>(a, t, n3, r, n6, nullptr, 0, w.bhat.template as<cplx<T>>(), n3,
+                                                    nullptr, nullptr, 0, nullptr, nullptr);
+    return after_launch("e_from_h_kernel");
+  }
+
+  // out = [x1; x2] with x1 = w.x and x2 = (r2 - z curlE(x1)) / a22
+  fdtd_status recover(Work<T> &w, const std::vector<std::complex<double>> &zs, cplx<T> *out) {
+    const int nb = (int)zs.size();
+    const int64_t n3 = 3 * nc, n6 = 6 * nc;
+    std::vector<std::complex<double>> negz(nb);
+    for (int b = 0; b < nb; ++b) negz[b] = -zs[b];
+    cplx<T> *x = w.x.template as<cplx<T>>(), *r = w.r.template as<cplx<T>>();
+    for (int b = 0; b < nb; ++b)
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(out + b * n6, x + b * n3, sizeof(cplx<T>) * n3, cudaMemcpyDeviceToDevice, s));
+    OpArgs<T> ah = make_op<T>(g, o.dt0, zs, negz);
+    // h_from_e writes its output with stride tstride; point it at the H half of out
+    h_from_e_kernel<T><<<dim3(nblk, nb), MB, 0, s>>>(ah, x, n3, nullptr, 0, r + n3, n6, out + n3, n6, nullptr);
+    return after_launch("h_from_e_kernel");
+  }
+
+  // S(z_b) x1 = bhat_b (w.bhat) -> w.x.  COCG (MOR_SOLVER_COCG, AUTO on FP32
+  // grids); the paper's CGS (AUTO on FP64 grids, falling back to BiCGSTAB for
+  // the whole block when a right-hand side fails); or BiCGSTAB.
+  fdtd_status schur_solve(Work<T> &w, const std::vector<std::complex<double>> &zs) {
+    if (o.solver == MOR_SOLVER_COCG || (o.solver == MOR_SOLVER_AUTO && g->prec != FDTD_F64))
+      return schur_cocg(w, zs);
+    if (o.solver != MOR_SOLVER_AUTO) return schur_krylov(w, zs, o.solver);
+    const bool nc0 = noconv;
+    const int it0 = max_iters;
+    const double r0 = max_resid;
+    FDTD_CHECK(schur_krylov(w, zs, MOR_SOLVER_CGS));
+    if (!last_failed) return FDTD_OK;
+    noconv = nc0; max_iters = it0; max_resid = r0;
+    fallbacks += 1;
+    return schur_krylov(w, zs, MOR_SOLVER_BICGSTAB);
+  }
+
+  // COCG with the gradient-corrected preconditioner inside a refinement loop:
+  // x (FP64) starts at 0; each outer step forms the true residual
+  // r = bhat - S x in FP64, stops when |r| <= tol |bhat| (Sec. IV-B's
+  // criterion, on the FP64 residual), else solves S d = r with COCG in the
+  // field type to a relative kInnerTol (FDTD_F32) and adds d to x.  With
+  // FDTD_F64 fields the inner solve goes straight to the requested tolerance.
+  // o.maxit caps the inner iterations of one shifted solve (all outer steps).
+  static constexpr double kInnerTol = 1e-2;
+  static constexpr int kMaxOuter = 8;
+
+  fdtd_status schur_cocg(Work<T> &w, const std::vector<std::complex<double>> &zs) {
+    const int nb = (int)zs.size();
+    const int64_t n3 = 3 * nc;
+    std::vector<std::complex<double>> one(nb, 1.0), zz(zs);
+    dim3 grid2(nblk, nb);
+    OpArgs<T> ap = make_op<T>(g, o.dt0, zs, zz);    // e_from_h half: cz = z
+    OpArgs<T> ah1 = make_op<T>(g, o.dt0, zs, one);  // h_from_e half: cz = 1
+    cplx<T> *t = w.t.template as<cplx<T>>(), *bh = w.bhat.template as<cplx<T>>();
+    FDTD_CHECK(w.x64.alloc(sizeof(cplx<double>) * nb * n3, s));
+    FDTD_CHECK(w.t64.alloc(sizeof(cplx<double>) * nb * n3, s));
+    FDTD_CHECK(w.phi.alloc(sizeof(cplx<T>) * nb * nc, s));
+    FDTD_CHECK(w.dN.alloc(sizeof(cplx<T>) * nb * nc, s));
+    FDTD_CHECK(w.upd.alloc(sizeof(int) * kMaxRhs, s));
+    if (!w.tickets.ptr) {
+      FDTD_CHECK(w.tickets.alloc(sizeof(unsigned) * 2 * kMaxRhs, s));
+      FDTD_CHECK_CUDA(cudaMemsetAsync(w.tickets.ptr, 0, sizeof(unsigned) * 2 * kMaxRhs, s));
     }
+    unsigned *tk = w.tickets.template as<unsigned>();
+    cplx<double> *x64 = w.x64.template as<cplx<double>>(), *t64 = w.t64.template as<cplx<double>>();
+    cplx<T> *phi = w.phi.template as<cplx<T>>(), *dN = w.dN.template as<cplx<T>>();
+    cplx<T> *P = w.P.template as<cplx<T>>(), *x = w.x.template as<cplx<T>>(), *rr = w.rr.template as<cplx<T>>();
+    cplx<T> *zv = w.u.template as<cplx<T>>(), *p = w.p.template as<cplx<T>>(), *q = w.q.template as<cplx<T>>();
+    CgsScal *sc = w.sc.template as<CgsScal>();
+    double *part = w.partials.template as<double>();
+    int *upd = w.upd.template as<int>();
+    const int eblk = std::min(nblk, 152 * 8);
+    dim3 gridE(eblk, nb);
+    jacobi_kernel<T><<<grid2, MB, 0, s>>>(ap, P, n3);
+    FDTD_CHECK(after_launch("jacobi_kernel"));
+    cocg_dn_kernel<T><<<grid2, MB, 0, s>>>(ap, dN);
+    FDTD_CHECK(after_launch("cocg_dn_kernel"));
+    FDTD_CHECK_CUDA(cudaMemsetAsync(x64, 0, sizeof(cplx<double>) * nb * n3, s));
+    const bool trace = getenv("FDTDMOR_TRACE") != nullptr;
+    auto scal_on = [&](cudaStream_t st, int mode) -> fdtd_status {
+      solver_scalars_kernel<<<1, 32 * nb, 0, st>>>(nb, nblk, part, sc, mode, -1.0, 0, 0);
+      return after_launch("solver_scalars_kernel");
+    };
+    const int astride = (int)(sizeof(CgsScal) / sizeof(int));
+    // one-pass Schur apply (FDTDMOR_SCHUR=pair selects the two-kernel form)
+    const char *sch = getenv("FDTDMOR_SCHUR");
+    const bool fused = !(sch && std::string(sch) == "pair");
+    const SchurShape shp = schur_shape(g, nb);
+    const int *act = reinterpret_cast<const int *>(reinterpret_cast<const char *>(sc) + offsetof(CgsScal, active));
+    auto iteration = [&](cudaStream_t st) -> fdtd_status {
+      cocg_update_p_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, zv, p, n3);
+      FDTD_CHECK(after_launch("cocg_update_p_kernel"));
+      if (fused) {
+        schur_fused_kernel<T, true><<<dim3(nb, shp.ntx * shp.nty, shp.nchunk), kSThreads, 0, st>>>(
+            ap, p, q, n3, shp.ntx, shp.zchunk, sc, part, tk);
+        FDTD_CHECK(after_launch("schur_fused_kernel"));
+      } else {
+        h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, p, n3, nullptr, 0, nullptr, 0, t, n3, act, astride);
+        FDTD_CHECK(after_launch("h_from_e_kernel"));
+        e_from_h_kernel<T, EM_APPLY_VDOT><<<grid2, MB, 0, st>>>(ap, t, n3, p, n3, nullptr, 0, q, n3, nullptr, nullptr,
+                                                                n3, sc, part, tk);
+        FDTD_CHECK(after_launch("e_from_h_kernel"));
+      }
+      cocg_node_kernel<T, false><<<grid2, MB, 0, st>>>(ap, rr, q, n3, dN, phi, sc);
+      FDTD_CHECK(after_launch("cocg_node_kernel"));
+      cocg_edge_kernel<T, false><<<grid2, MB, 0, st>>>(ap, rr, q, x, p, phi, P, zv, n3, sc, part, tk + kMaxRhs);
+      return after_launch("cocg_edge_kernel");
+    };
+    const int poll = 16;
+    if (!cocg_graph && !getenv("FDTDMOR_NO_GRAPH")) {
+      if (!cap) FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      const int64_t before = fdtd_launch_count(0);
+      FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      fdtd_status st = FDTD_OK;
+      for (int k = 0; k < poll && st == FDTD_OK; ++k) st = iteration(cap);
+      cocg_graph_launches = fdtd_launch_count(0) - before;
+      add_launches(-cocg_graph_launches);  // captured, not launched
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+      if (st != FDTD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "COCG graph capture");
+      const cudaError_t e2 = cudaGraphInstantiate(&cocg_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) { cocg_graph = nullptr; return cuda_fail(e2, "COCG graph instantiate"); }
+    }
+    std::vector<CgsScal> hsc(nb);
+    std::vector<double> bn(nb, 0.0), rn(nb, 0.0);
+    std::vector<int> used(nb, 0), capped(nb, 0), need(nb, 0);
+    const bool f64 = sizeof(T) == 8;
+    int outer = 0;
+    for (;; ++outer) {
+      // true residual in FP64 (x64 = 0 on the first pass: r = bhat)
+      resid64_h_kernel<T><<<grid2, MB, 0, s>>>(ah1, x64, t64, n3);
+      FDTD_CHECK(after_launch("resid64_h_kernel"));
+      resid64_e_kernel<T><<<grid2, MB, 0, s>>>(ap, t64, x64, n3, bh, rr, part);
+      FDTD_CHECK(after_launch("resid64_e_kernel"));
+      solver_scalars_kernel<<<1, 32 * nb, 0, s>>>(nb, nblk, part, sc, SM_NORM, 1.0, 1, 0);
+      FDTD_CHECK(after_launch("solver_scalars_kernel"));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+      bool any = false;
+      for (int b = 0; b < nb; ++b) {
+        rn[b] = std::sqrt(std::max(hsc[b].rn2, 0.0));
+        if (outer == 0) bn[b] = rn[b];
+        need[b] = bn[b] > 0 && std::isfinite(rn[b]) && rn[b] > o.tol * bn[b] && !capped[b] && used[b] < o.maxit;
+        any |= need[b] != 0;
+      }
+      if (trace) {
+        fprintf(stderr, "[cocg] outer %d true residual", outer);
+        for (int b = 0; b < nb; ++b) fprintf(stderr, " %.3e", bn[b] > 0 ? rn[b] / bn[b] : 0.0);
+        fprintf(stderr, "\n");
+      }
+      if (!any || outer >= kMaxOuter) break;
+      // inner solve S d = r for the right-hand sides still above tolerance
+      for (int b = 0; b < nb; ++b) {
+        CgsScal &c = hsc[b];
+        c = CgsScal{};
+        c.active = need[b];
+        c.itol = f64 ? std::min(0.5, 0.5 * o.tol * bn[b] / std::max(rn[b], 1e-300))
+                     : std::max(kInnerTol, std::min(0.5, 0.5 * o.tol * bn[b] / std::max(rn[b], 1e-300)));
+        c.imaxit = std::max(1, o.maxit - used[b]);
+      }
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(sc, hsc.data(), sizeof(CgsScal) * nb, cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(upd, need.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaMemsetAsync(x, 0, sizeof(cplx<T>) * nb * n3, s));
+      FDTD_CHECK_CUDA(cudaMemsetAsync(p, 0, sizeof(cplx<T>) * nb * n3, s));
+      cocg_node_kernel<T, true><<<grid2, MB, 0, s>>>(ap, rr, nullptr, n3, dN, phi, sc);
+      FDTD_CHECK(after_launch("cocg_node_kernel"));
+      cocg_edge_kernel<T, true><<<grid2, MB, 0, s>>>(ap, rr, nullptr, nullptr, nullptr, phi, P, zv, n3, sc, part,
+                                                     nullptr);
+      FDTD_CHECK(after_launch("cocg_edge_kernel"));
+      FDTD_CHECK(scal_on(s, SM_INIT));
+      for (int it = 0; it < o.maxit + poll; it += poll) {
+        if (cocg_graph) {
+          FDTD_CHECK_CUDA(cudaGraphLaunch(cocg_graph, s));
+          add_launches(cocg_graph_launches);
+        } else {
+          for (int k = 0; k < poll; ++k) FDTD_CHECK(iteration(s));
+        }
+        FDTD_CHECK_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(CgsScal) * nb, cudaMemcpyDeviceToHost, s));
+        FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+        bool act_any = false;
+        for (auto &c : hsc) act_any |= c.active != 0;
+        if (trace) {
+          fprintf(stderr, "[cocg] it %d", it + poll);
+          for (auto &c : hsc) fprintf(stderr, " %.3e%s", c.bn2 > 0 ? std::sqrt(c.rn2 / c.bn2) : 0.0, c.active ? "" : "*");
+          fprintf(stderr, "\n");
+        }
+        if (!act_any) break;
+      }
+      for (int b = 0; b < nb; ++b) {
+        if (!need[b]) continue;
+        used[b] += hsc[b].iters;
+        if (hsc[b].status != 0) capped[b] = 1;  // iteration cap or breakdown: keep x, stop refining
+      }
+      const int eblk2 = std::min(nblk, 152 * 8);
+      acc64_kernel<T><<<dim3(eblk2, nb), MB, 0, s>>>(n3, upd, x, x64, n3);
+      FDTD_CHECK(after_launch("acc64_kernel"));
+    }
+    outer_max = std::max(outer_max, outer);
+    last_failed = false;
+    rhs_failed.assign(nb, 0);
+    rhs_iters = used;
+    rhs_resid.assign(nb, 0.0);
+    for (int b = 0; b < nb; ++b) {
+      max_iters = std::max(max_iters, used[b]);
+      if (bn[b] > 0) rhs_resid[b] = rn[b] / bn[b];
+      if (bn[b] > 0) max_resid = std::max(max_resid, rn[b] / bn[b]);
+      if (bn[b] > 0 && !(rn[b] <= o.tol * bn[b])) { noconv = true; last_failed = true; rhs_failed[b] = 1; }
+    }
+    from64_kernel<T><<<dim3(eblk, nb), MB, 0, s>>>(n3, x64, n3, x, n3);
+    return after_launch("from64_kernel");
+  }
+
+  fdtd_status schur_krylov(Work<T> &w, const std::vector<std::complex<double>> &zs, int solver) {
+    const int nb = (int)zs.size();
+    const int64_t n3 = 3 * nc;
+    std::vector<std::complex<double>> one(nb, 1.0), zz(zs);
+    dim3 grid2(nblk, nb);
+    cplx<T> *t = w.t.template as<cplx<T>>();
     // S x = a11 x + z curlH(curlE(x)/a22): the curlE half carries no factor,
     // the curlH half carries z.
     OpArgs<T> ap = make_op<T>(g, o.dt0, zs, zz);       // e_from_h half: cz = z
@@ -896,20 +1567,16 @@ struct BasisBuilder {
     FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
     last_failed = false;
     rhs_failed.assign(nb, 0);
+    rhs_iters.assign(nb, 0);
+    rhs_resid.assign(nb, 0.0);
     for (int b = 0; b < nb; ++b) {
       const CgsScal &x2 = hsc[b];
+      rhs_iters[b] = x2.iters;
+      if (x2.bn2 > 0) rhs_resid[b] = std::sqrt(x2.rn2 / x2.bn2);
       max_iters = std::max(max_iters, x2.iters);
       if (x2.bn2 > 0) max_resid = std::max(max_resid, std::sqrt(x2.rn2 / x2.bn2));
       if (x2.status != 0 || x2.active) { noconv = true; last_failed = true; rhs_failed[b] = 1; }
     }
-    // out = [x1; x2], x2 = (r2 - z curlE(x1)) / a22
-    for (int b = 0; b < nb; ++b) {
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(out + b * n6, x + b * n3, sizeof(cplx<T>) * n3, cudaMemcpyDeviceToDevice, s));
-    }
-    OpArgs<T> ah = make_op<T>(g, o.dt0, zs, negz);
-    // h_from_e writes its output with stride tstride; point it at the H half of out
-    h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah, x, n3, nullptr, 0, r + n3, n6, out + n3, n6, nullptr);
-    FDTD_CHECK(after_launch("h_from_e_kernel"));
     return FDTD_OK;
   }
 
@@ -968,6 +1635,42 @@ struct BasisBuilder {
   }
 };
 
+
+// A4 on its own: S(z_b) x_b = b_b for nb given right-hand sides (b, x: device
+// [nb][3 nc] complex in the grid's type).
+template <typename T>
+static fdtd_status shifted_solve_t(fdtd_grid *g, const mor_opts &o, const std::vector<std::complex<double>> &zs,
+                                   const void *b, void *x, int *iters, double *resid, cudaStream_t s) {
+  FDTD_CHECK(ensure_edge_props(g, s));
+  const int nb = (int)zs.size();
+  const int64_t n3 = 3 * g->nc;
+  BasisBuilder<T> bb(g, o, s);
+  Work<T> w;
+  w.nb = nb;
+  const size_t cb = sizeof(cplx<T>);
+  struct Rel {
+    Work<T> &w;
+    cudaStream_t s;
+    ~Rel() {
+      cudaStreamSynchronize(s);
+      for (DevBuf *d : {&w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc,
+                        &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets})
+        d->release(s);
+    }
+  } rel{w, s};
+  for (DevBuf *d : {&w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t}) FDTD_CHECK(d->alloc(cb * nb * n3, s));
+  FDTD_CHECK(w.partials.alloc(sizeof(double) * 3 * nb * (size_t)std::max(bb.nblk, 152 * 16), s));
+  FDTD_CHECK(w.sc.alloc(sizeof(CgsScal) * nb, s));
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(w.bhat.ptr, b, cb * nb * n3, cudaMemcpyDefault, s));
+  FDTD_CHECK(bb.schur_solve(w, zs));
+  FDTD_CHECK_CUDA(cudaMemcpyAsync(x, w.x.ptr, cb * nb * n3, cudaMemcpyDefault, s));
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < nb; ++i) {
+    if (iters) iters[i] = i < (int)bb.rhs_iters.size() ? bb.rhs_iters[i] : 0;
+    if (resid) resid[i] = i < (int)bb.rhs_resid.size() ? bb.rhs_resid[i] : 0.0;
+  }
+  return bb.noconv ? FDTD_ENOCONV : FDTD_OK;
+}
 
 template <typename T>
 static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s, mor_basis *B) {
@@ -1205,7 +1908,8 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
     (half == 0 ? B->q1 : B->q2) = qc;
   }
   FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
-  for (DevBuf *d : {&w.v, &w.r, &w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc, &w.dots, &w.dpart, &chains, &xs, &tmp})
+  for (DevBuf *d : {&w.v, &w.r, &w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc,
+                    &w.dots, &w.dpart, &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets, &chains, &xs, &tmp})
     d->release(s);
   B->max_iters = bb.max_iters;
   B->max_resid = bb.max_resid;
@@ -1249,6 +1953,20 @@ fdtd_status mor_build_basis(fdtd_grid *g, const mor_opts *o, fdtd_stream_t strea
   return st;
 }
 
+fdtd_status mor_shifted_solve(fdtd_grid *g, const mor_opts *o, int nb, const double *z, const void *b, void *x,
+                              int *iters, double *resid, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g && o && z && b && x, "mor_shifted_solve: NULL argument");
+  FDTD_REQUIRE(nb >= 1 && nb <= kMaxRhs, "mor_shifted_solve: nb must be 1..%d", kMaxRhs);
+  FDTD_REQUIRE(o->dt0 > 0 && o->tol > 0 && o->maxit >= 1, "mor_shifted_solve: need dt0 > 0, tol > 0, maxit >= 1");
+  std::vector<std::complex<double>> zs(nb);
+  for (int i = 0; i < nb; ++i) zs[i] = std::complex<double>(z[2 * i], z[2 * i + 1]);
+  cudaStream_t s = (cudaStream_t)stream;
+  const fdtd_status st = g->prec == FDTD_F64 ? shifted_solve_t<double>(g, *o, zs, b, x, iters, resid, s)
+                                             : shifted_solve_t<float>(g, *o, zs, b, x, iters, resid, s);
+  if (st == FDTD_ENOCONV) set_error("mor_shifted_solve: a right-hand side missed tol");
+  return st;
+}
+
 fdtd_status mor_basis_info(const mor_basis *b, int *q1, int *q2, int *max_iters, double *max_resid) {
   FDTD_REQUIRE(b, "mor_basis_info: NULL basis");
   if (q1) *q1 = b->q1;
@@ -1286,12 +2004,20 @@ fdtd_status mor_schur_apply(fdtd_grid *g, double dt0, int nb, const double *z, c
   const int64_t n3 = 3 * g->nc;
   const int nblk = (int)((g->nc + MB - 1) / MB);
   const dim3 grid2(nblk, nb);
+  const char *sch = getenv("FDTDMOR_SCHUR");
+  const bool pair = sch && std::string(sch) == "pair";
   auto run = [&](auto tag) -> fdtd_status {
     using T = decltype(tag);
-    DevBuf t;
-    FDTD_CHECK(t.alloc((size_t)nb * n3 * sizeof(cplx<T>), s));
     const OpArgs<T> ah1 = make_op<T>(g, dt0, zs, one), ap = make_op<T>(g, dt0, zs, zs);
     const cplx<T> *xv = static_cast<const cplx<T> *>(x);
+    if (!pair) {
+      const SchurShape shp = schur_shape(g, nb);
+      schur_fused_kernel<T, false><<<dim3(nb, shp.ntx * shp.nty, shp.nchunk), kSThreads, 0, s>>>(
+          ap, xv, static_cast<cplx<T> *>(y), n3, shp.ntx, shp.zchunk, nullptr, nullptr, nullptr);
+      return after_launch("schur_fused_kernel");
+    }
+    DevBuf t;
+    FDTD_CHECK(t.alloc((size_t)nb * n3 * sizeof(cplx<T>), s));
     h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, xv, n3, nullptr, 0, nullptr, 0, t.as<cplx<T>>(), n3, nullptr);
     fdtd_status st = after_launch("h_from_e_kernel");
     if (st == FDTD_OK) {

@@ -26,6 +26,11 @@ template <typename T> __host__ __device__ __forceinline__ cplx<T> cdiv(cplx<T> a
   return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
 }
 template <typename T, typename U> __host__ __device__ __forceinline__ cplx<T> ccast(cplx<U> a) { return {(T)a.re, (T)a.im}; }
+// FP32 coefficient times an FP64 complex value (the FP64 residual of the
+// refinement loop reads the FP32 axis tables and material properties).
+__host__ __device__ __forceinline__ cplx<double> operator*(float s, cplx<double> a) {
+  return {(double)s * a.re, (double)s * a.im};
+}
 
 // Geometry view for stencils over the storage layout.
 template <typename T>

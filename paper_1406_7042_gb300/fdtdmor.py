@@ -53,7 +53,7 @@ class MorOpts(C.Structure):
 
 
 MOR_ORTH = {"native": 0, "tf32": 1, "bf16": 2}
-MOR_SOLVER = {"auto": 0, "cgs": 1, "bicgstab": 2}
+MOR_SOLVER = {"auto": 0, "cgs": 1, "bicgstab": 2, "cocg": 3}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -120,6 +120,8 @@ _SIGS = [
                            C.c_void_p, C.c_void_p, C.c_void_p]),
     ("mor_schur_apply", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    ("mor_shifted_solve", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_int, C.POINTER(C.c_double), C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]),
     ("mor_build_basis", C.c_int, [C.c_void_p, C.POINTER(MorOpts), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_basis_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_double)]),
@@ -514,6 +516,30 @@ def schur_apply(grid: "Grid", dt0: float, z, x, out=None, stream=None):
         out = torch.empty_like(x)
     check(lib().mor_schur_apply(grid.h, float(dt0), int(zz.size), zarr, _dptr(x), _dptr(out), _stream_ptr(stream)))
     return out
+
+
+def shifted_solve(grid: "Grid", dt0: float, z, b, tol: float = 1e-4, maxit: int = 20000, solver: str = "auto",
+                  out=None, stream=None, allow_noconv: bool = False):
+    """x_b = S(z_b)^{-1} b_b (mor_shifted_solve): b complex (nb, 3, nz, ny, nx)
+    device tensor of the grid's precision; z: nb complex numbers.  Returns
+    (x, iterations per RHS, final relative residual per RHS)."""
+    import torch
+    L_ = lib()
+    o = MorOpts()
+    check(L_.mor_opts_default(C.byref(o)))
+    o.dt0, o.tol, o.maxit, o.solver = float(dt0), float(tol), int(maxit), MOR_SOLVER[solver]
+    zz = np.asarray(z, np.complex128).ravel()
+    zarr = (C.c_double * (2 * zz.size))(*[v for c in zz for v in (c.real, c.imag)])
+    b = b.contiguous()
+    if out is None:
+        out = torch.empty_like(b)
+    it = (C.c_int * zz.size)()
+    rs = (C.c_double * zz.size)()
+    st = L_.mor_shifted_solve(grid.h, C.byref(o), int(zz.size), zarr, _dptr(b), _dptr(out), it, rs,
+                              _stream_ptr(stream))
+    if st != FDTD_OK and not (allow_noconv and st == FDTD_ENOCONV):
+        check(st)
+    return out, list(it), list(rs)
 
 
 def dft(y, dt: float, freqs, hann: bool = False, stream=None) -> np.ndarray:

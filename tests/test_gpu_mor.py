@@ -6,6 +6,8 @@ inputs of that stage (so a mismatch points at one kernel), and the pipeline
 end to end against the oracle pipeline."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -203,6 +205,136 @@ def test_shifted_solve_parity_lossy_multiport(prec, center):
         cosines = np.linalg.svd(Vg.T @ Vo, compute_uv=False)
         assert Vg.shape[1] == Vo.shape[1]
         assert cosines.min() > 1 - (1e-10 if prec == "f64" else 1e-6), cosines
+
+
+@pytest.mark.parametrize("center", [True, False])
+def test_cocg_f64_matches_oracle(center):
+    """The COCG path (volume-weighted unconjugated products, gradient-corrected
+    preconditioner) in FP64 solves the same shifted systems as the oracle's
+    sparse LU: one block moment per port, principal cosines to 1e-10."""
+    g = _lossy_ragged()
+    s = yee.assemble(g)
+    dt0 = 0.99 * yee.cfl_dt(g)
+    L, q = (0, 2) if center else (1, 4)
+    ob = mor.sprim_basis(s, dt0, q, L, 1.1, 60e9, include_center=center, defl_tol=1e-6)
+    grid = F.Grid(g, "f64")
+    gb = F.Basis(grid, q, dt0, L, 1.1, 60e9, include_center=center, tol=1e-12, defl_tol=1e-6, solver="cocg")
+    assert gb.status == F.FDTD_OK
+    for which, comps, Vo in ((1, "E", ob.V1), (2, "H", ob.V2)):
+        Vg = _vectors_to_oracle(s, gb.V(which).cpu().numpy(), comps)
+        cosines = np.linalg.svd(Vg.T @ Vo, compute_uv=False)
+        assert Vg.shape[1] == Vo.shape[1]
+        assert cosines.min() > 1 - 1e-10, cosines
+
+
+def _graded20():
+    """The bench cavity's construction (0.5 mm cells, z graded to a 2-cell
+    0.05 mm slab of eps_r 4, lossy seeded blocks) at 20^3, small enough for
+    the oracle's sparse LU to factorise three shifted systems in a minute."""
+    g = W.cavity_graded(20)
+    s = yee.assemble(g)
+    dt0 = 0.99 * yee.cfl_dt(g)
+    fmax = 15e9
+    return g, s, dt0, fmax, 1.0 + np.pi * fmax * dt0
+
+
+def test_cocg_refined_solves_reach_paper_tolerance():
+    """FP32 fields on the finely graded cavity: inside the basis build the FP64
+    refinement takes every shifted solve to a true residual <= 1e-4
+    (Sec. IV-B), which FP32 arithmetic alone cannot reach there."""
+    g, s, dt0, fmax, M = _graded20()
+    grid = F.Grid(g, "f32")
+    gb = F.Basis(grid, 20, dt0, 2, M, fmax, tol=1e-4, defl_tol=1e-5)
+    inf = gb.info()
+    assert gb.status == F.FDTD_OK
+    assert 0 < inf["max_resid"] <= 1e-4, inf
+    assert inf["max_iters"] < 1000, inf
+
+
+def _storage_to_live(s, x):
+    """(nb, 3, nz, ny, nx) storage-layout E blocks -> (nb, Ne) live unknowns."""
+    return np.stack([np.concatenate([x[b, c][s.e_mask[c]] for c in range(3)]) for b in range(x.shape[0])])
+
+
+def _live_to_storage(s, v):
+    nz, ny, nx = s.shape
+    out = np.zeros((v.shape[0], 3, nz, ny, nx), v.dtype)
+    for b in range(v.shape[0]):
+        off = 0
+        for c in range(3):
+            n = int(s.e_mask[c].sum())
+            out[b, c][s.e_mask[c]] = v[b, off:off + n]
+            off += n
+    return out
+
+
+@pytest.mark.parametrize("case,prec,solver,tol,fwd_tol", [
+    ("ragged", "f64", "cgs", 1e-10, 1e-7),
+    ("ragged", "f64", "bicgstab", 1e-10, 1e-7),
+    ("ragged", "f64", "cocg", 1e-10, 1e-7),
+    ("ragged", "f32", "cocg", 1e-4, 2e-3),
+    ("graded", "f32", "cocg", 1e-4, 2e-3),
+])
+def test_shifted_solve_matches_lu(case, prec, solver, tol, fwd_tol):
+    """A4 through mor_shifted_solve: S(z) x = b for seeded complex b at points
+    of the arc of Eq. (distrib), against the oracle's sparse LU of the Schur
+    complement (Eqs. (reduced_linear_system_solution1/2)), element by
+    element.  The GPU works in per-volume rows, S_gpu = V_e^{-1} S."""
+    if case == "ragged":
+        g = _lossy_ragged()
+        s = yee.assemble(g)
+        dt0 = 0.99 * yee.cfl_dt(g)
+        zs = [1.1 + 0j, 1.1 * np.exp(1j * 2 * np.pi * 60e9 * dt0)]
+    else:
+        g, s, dt0, fmax, M = _graded20()
+        zs = [M + 0j, M * np.exp(1j * 2 * np.pi * fmax * dt0)]
+    rng = np.random.default_rng(7)
+    bl = rng.standard_normal((len(zs), s.Ne)) + 1j * rng.standard_normal((len(zs), s.Ne))
+    grid = F.Grid(g, prec)
+    cdt = torch.complex128 if prec == "f64" else torch.complex64
+    bt = torch.tensor(_live_to_storage(s, bl), dtype=cdt, device="cuda")
+    x, iters, resid = F.shifted_solve(grid, dt0, zs, bt, tol=tol, solver=solver)
+    xl = _storage_to_live(s, x.cpu().numpy().astype(np.complex128))
+    for b, z in enumerate(zs):
+        a11, a22 = mor.schur_blocks(s, dt0, z)
+        K = s.K.astype(np.complex128)
+        S = (sp.diags(a11) + z * K @ sp.diags(1.0 / a22) @ K.T).tocsc()
+        xo = sla.splu(S).solve(s.vol_e * bl[b])
+        assert resid[b] <= tol, (b, resid, iters)
+        assert np.linalg.norm(xl[b] - xo) <= fwd_tol * np.linalg.norm(xo), (b, np.linalg.norm(xl[b] - xo) / np.linalg.norm(xo))
+
+
+def test_reduced_model_matches_oracle_at_bench_settings():
+    """Separates the GPU path's error from the method's on a config-2-shaped
+    grid at the bench's settings: FP32 fields, COCG with FP64 refinement to
+    tol 1e-4, L = 2, M = 1 + pi fmax dt0, q = 60.  Near z = 1 the later chain
+    vectors are dependent to below the FP32 solves' error, so the GPU basis
+    keeps other columns than the exact one; what must agree is the model: its
+    probe error against the oracle's full-order run at s = 0.99 and s = 19.8
+    (same physical time) is at most the oracle reduction's own (sparse-LU
+    chains, CGS2, projection, perturbation, reduced leap-frog) plus 1e-3."""
+    g, s, dt0, fmax, M = _graded20()
+    q, L, nref = 60, 2, 4000
+    ob = mor.sprim_basis(s, dt0, q, L, M, fmax, defl_tol=1e-5)
+    red = mor.project(s, ob.V1, ob.V2)
+    uref = W.excitation(g, 10e9, 10e9, dt0, nref)
+    yref = yee.Stepper(s, dt0).run(uref)[0]
+    g32 = F.Grid(g, "f32")
+    b32 = F.Basis(g32, q, dt0, L, M, fmax, tol=1e-4, defl_tol=1e-5)
+    assert b32.status == F.FDTD_OK and b32.info()["max_resid"] <= 1e-4
+    m32 = F.Model(g32, b32)
+    for k in (1, 20):
+        dt = k * dt0
+        n = nref // k
+        u = W.excitation(g, 10e9, 10e9, dt, n)
+        ysub = yref[k - 1::k][:n]
+        pr, _, _ = mor.perturb(red, dt, GAMMA)
+        yo = mor.reduced_run(pr, dt, u)
+        m32.perturb(dt, GAMMA)
+        y32 = m32.run(torch.tensor(u, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+        e_or, e_32 = mor.rel_l2(yo, ysub), mor.rel_l2(y32, ysub)
+        print(f"s = {0.99 * k:.2f}: oracle model {e_or:.3e}, GPU FP32 model {e_32:.3e} against the full-order run")
+        assert e_32 <= e_or + TOL_RED_F32, (k, e_32, e_or)
 
 
 def test_lossy_multiport_moments_and_stages_f64():
