@@ -267,6 +267,7 @@ def run_ours(args):
         red_ms = sum(stage[k] for k in ("basis_ms", "project_ms", "perturb_ms", "run_ms"))
         inf = state["basis"].info()
         line["reduce_run"] = dict(stage, reduce_run_ms=round(red_ms, 3),
+                                  run_us_per_step=round(1e3 * stage["run_ms"] / max(1, nred), 3),
                                   fdtd_ms=round(fdtd_ms / args.steps, 3),
                                   speedup_vs_fdtd=round((fdtd_ms / args.steps) / red_ms, 4),
                                   probe_err_vs_fdtd=round(state["err"], 6), q1=inf["q1"], q2=inf["q2"],
@@ -496,6 +497,34 @@ def hbm_grid_measure(F, W, hbm, nsteps=200):
             "bytes_per_cell": bytes_per_cell}
 
 
+def reduced_run_measure(F, W, q_list=(200, 400), nsteps=20000):
+    """Reduced leap-frog (mor_run) microseconds per step for FP32 models of
+    order q (random SPD-projected models are not needed: the step matrices of
+    a real basis of the 64^3 graded cavity at q columns)."""
+    import torch
+    wl = _workload()
+    grid = F.Grid(wl.grid, "f32")
+    dt0 = wl.s_ref * grid.cfl_dt()
+    out = {}
+    for q in q_list:
+        basis = F.Basis(grid, q, dt0, wl.L, wl.M, wl.fmax, tol=1e-3, defl_tol=1e-7, allow_noconv=True)
+        model = F.Model(grid, basis)
+        model.perturb(20 * dt0)
+        u = torch.tensor(W.excitation(wl.grid, wl.f0, wl.bw, 20 * dt0, nsteps), dtype=torch.float32, device="cuda")
+        y = torch.empty((nsteps, grid.p), dtype=torch.float32, device="cuda")
+        model.run(u[:100].contiguous(), y[:100])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        model.run(u, y)
+        b.record()
+        torch.cuda.synchronize()
+        inf = basis.info()
+        out[f"q={q}"] = {"q1": inf["q1"], "q2": inf["q2"], "us_per_step": round(1e3 * a.elapsed_time(b) / nsteps, 3)}
+        del model, basis
+    return out
+
+
 def only_yee(args):
     """Just the Yee kernel on one workload grid (the small command used for ncu captures)."""
     import torch
@@ -559,6 +588,7 @@ def main():
     ap.add_argument("--yee-steps", type=int, default=20)
     ap.add_argument("--only-basis", action="store_true")
     ap.add_argument("--only-batch", action="store_true")
+    ap.add_argument("--only-run", action="store_true", help="reduced-run microseconds per step at q = 200, 400")
     ap.add_argument("--only-tensor", action="store_true")
     ap.add_argument("--only-gram", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="with --only-yee: tune the tile first")
@@ -593,6 +623,11 @@ def main():
         from paper_1406_7042_gb300 import workloads as W
         print(json.dumps({"tensor_gram": tensor_gram_measure(F, _peaks()), "precision_study": precision_study(F, W),
                           "precision_study_absorbing": precision_study(F, W, absorbing=True)}))
+        return 0
+    if args.only_run:
+        from paper_1406_7042_gb300 import fdtdmor as F
+        from paper_1406_7042_gb300 import workloads as W
+        print(json.dumps({"only_run": reduced_run_measure(F, W)}))
         return 0
     if args.only_batch:
         from paper_1406_7042_gb300 import fdtdmor as F

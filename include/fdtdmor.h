@@ -375,6 +375,9 @@ FDTD_API fdtd_status mor_perturb(mor_model *model, double dt, double gamma, int 
 /* A8 -- reduced leap-frog, Eq. (reducedMNAform) in block form, nsteps steps at
  * the dt of the last mor_perturb, in one persistent kernel:
  * e <- Pe e - Qe h + be u^{n+1}, h <- Ph h + Qh e + bh u^{n+1}, y^n = C~ e.
+ * Step matrices that fit one CTA's shared memory run on one CTA; larger ones
+ * on a thread-block cluster (up to 16 CTAs) holding row slices in shared
+ * memory and exchanging the state through distributed shared memory.
  * u: device [nsteps][m], y: device [nsteps][p] (grid type). */
 FDTD_API fdtd_status mor_run(mor_model *model, int64_t nsteps, const void *u, void *y,
                              int reset_state, fdtd_stream_t stream);

@@ -407,132 +407,236 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
 // ------------------------------------------- fused one-pass Schur apply
 // q = a11 p + z curlH(curlE(p) / a22) in one pass over memory: the H-part
 // intermediate t lives in shared memory only.  A CTA owns a tile of
-// kSX x kSY cells in x, y and marches a chunk of z planes upwards.  Per plane
-// k: warps 0..kSY compute t(k) = curlE(p)/a22 on rows j0-1 .. j0+kSY-1 of the
-// tile's 32 columns and warp kSY+1 on the -x halo column (i0-1), into the
-// plane-parity slot of the shared tile; after one barrier warps 1..kSY form q
-// at their own cells from t(k) (own, -x, -y neighbours) and t(k-1) (own
-// position, kept in registers).  Two parity slots make one barrier per plane
-// enough.  H edges outside the grid contribute zero, as in curl_h3.
+// kSX x kSY cells in x, y, a group of NB right-hand sides, and marches a
+// chunk of z planes upwards.  Per plane k: warps 0..kSY compute t(k) =
+// curlE(p)/a22 on rows j0-1 .. j0+kSY-1 of the tile's 32 columns and warp
+// kSY+1 on the -x halo column (i0-1), into the plane-parity slot of the shared
+// tile; after one barrier warps 1..kSY form q at their own cells from t(k)
+// (own, -x, -y neighbours) and t(k-1) (own position, kept in registers).  Two
+// parity slots make one barrier per plane enough.  Every thread issues the
+// loads of all NB right-hand sides of a plane (and the material properties of
+// both phases) before using them: the march is latency-bound, and NB
+// independent load streams per warp keep more of them in flight.  H edges
+// outside the grid contribute zero, as in curl_h3.
 // VDOT: partials of (p, q)_V and, with tickets, alpha = rho / (p, q)_V by
-// the last CTA of each right-hand side.  Grid: (nb, tiles, z chunks).
+// the last CTA of each right-hand side.  Grid: (RHS groups, tiles, z chunks).
 constexpr int kSX = 32, kSY = 8;
 constexpr int kSThreads = 32 * (kSY + 2);
 
-template <typename T, bool VDOT>
-__global__ void __launch_bounds__(kSThreads) schur_fused_kernel(OpArgs<T> a, const cplx<T> *__restrict__ p,
-                                                                cplx<T> *__restrict__ q, int64_t stride, int ntx,
-                                                                int zchunk, CgsScal *__restrict__ sc,
-                                                                double *__restrict__ partials,
-                                                                unsigned *__restrict__ tickets) {
-  __shared__ cplx<T> ts[2][3][kSY + 1][kSX + 1];
+template <typename T, bool VDOT, int NB>
+__global__ void __launch_bounds__(kSThreads, 2) schur_fused_kernel(OpArgs<T> a, int nb, const cplx<T> *__restrict__ p,
+                                                                   cplx<T> *__restrict__ q, int64_t stride, int ntx,
+                                                                   int zchunk, CgsScal *__restrict__ sc,
+                                                                   double *__restrict__ partials,
+                                                                   unsigned *__restrict__ tickets) {
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  cplx<T> *ts = reinterpret_cast<cplx<T> *>(ts_raw);  // [parity][r][c][row][col]
+  auto TS = [&](int par, int r, int c, int row, int col) -> cplx<T> & {
+    return ts[((((par * NB + r) * 3 + c) * (kSY + 1) + row) * (kSX + 1)) + col];
+  };
   __shared__ double sh[3 * 32];
-  const int b = blockIdx.x;
-  if (VDOT && sc && !sc[b].active) return;
+  const int b0 = blockIdx.x * NB;
+  bool act[NB];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    act[r] = b0 + r < nb && (!VDOT || !sc || sc[b0 + r].active);
+    any |= act[r];
+  }
+  if (!any) return;
   const Geo<T> &g = a.g;
   const int64_t nc = g.nc, sy = g.nx, sz = (int64_t)g.nx * g.ny;
   const int tile = blockIdx.y, i0 = (tile % ntx) * kSX, j0 = (tile / ntx) * kSY;
   const int k0 = blockIdx.z * zchunk, k1 = min(g.nz, k0 + zchunk);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // phase-1 position of this thread
-  int pi, pj, prow, pcol;
+  int pi, pj, prow, pcol;  // phase-1 position of this thread and its shared slot
   if (warp <= kSY) { pi = i0 + lane; pj = j0 - 1 + warp; prow = warp; pcol = lane + 1; }
   else { pi = i0 - 1; pj = j0 - 1 + lane; prow = lane; pcol = 0; }
-  const bool p1 = (warp <= kSY || lane <= kSY) && pi >= 0 && pi < g.nx && pj >= 0 && pj < g.ny;
-  const bool own = warp >= 1 && warp <= kSY && pi < g.nx && pj < g.ny;  // phase-2 owner (i = pi, j = pj)
-  const cplx<T> *pb = p + b * stride;
-  const cplx<T> z = a.z[b], zm1(z.re - T(1), z.im), zp1(z.re + T(1), z.im);
-  // t = curlE(p) / a22 at H edges of cell (i, j, kk); pe* return own E at kk
-  auto tcomp = [&](int i, int j, int kk, cplx<T> out[3], cplx<T> own_e[3]) {
-    const int64_t n = g.id(i, j, kk);
-    auto ld = [&](int64_t idx) { return pb[idx]; };
-    cplx<T> ce[3];
-    curl_e3<T, cplx<T>>(g, ld, i, j, kk, n, ce);
-    own_e[0] = pb[n]; own_e[1] = pb[nc + n]; own_e[2] = pb[2 * nc + n];
-    for (int c = 0; c < 3; ++c) {
-      const int64_t e = c * nc + n;
-      const T mu = a.mu[e];
-      cplx<T> o;
-      if (mu != T(0)) {
-        const cplx<T> a22 = (mu * a.inv_dt) * zm1 + (T(0.5) * a.sgm[e]) * zp1;
-        o = cdiv(ce[c], a22);
-      }
-      out[c] = o;
+  const bool writer = warp <= kSY || lane <= kSY;
+  const bool p1 = writer && pi >= 0 && pi < g.nx && pj >= 0 && pj < g.ny;
+  const bool own = warp >= 1 && warp <= kSY && pi < g.nx && pj < g.ny;  // phase-2 owner of (pi, pj)
+  const bool ip = pi + 1 < g.nx, jp = pj + 1 < g.ny;
+  cplx<T> zm1[NB], zp1[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const cplx<T> z = a.z[min(b0 + r, nb - 1)];
+    zm1[r] = cplx<T>(z.re - T(1), z.im);
+    zp1[r] = cplx<T>(z.re + T(1), z.im);
+  }
+  const T rx = p1 ? g.rd(0, pi) : T(0), ry = p1 ? g.rd(1, pj) : T(0);
+  const T rdx = own ? g.rdd(0, pi) : T(0), rdy = own ? g.rdd(1, pj) : T(0);
+  const int64_t n00 = p1 ? g.id(pi, pj, 0) : 0;
+  // own Ex, Ey of the position at the current plane, carried up the march
+  cplx<T> cex[NB], cey[NB], tpx[NB], tpy[NB];
+  auto load_carry = [&](int kk) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const cplx<T> *pb = p + (int64_t)(b0 + (act[r] ? r : 0)) * stride;
+      const int64_t n = n00 + kk * sz;
+      cex[r] = act[r] ? pb[n] : cplx<T>();
+      cey[r] = act[r] ? pb[nc + n] : cplx<T>();
     }
   };
-  cplx<T> tprev[3], pe[3], tk[3];
-  if (own && k0 > 0) tcomp(pi, pj, k0 - 1, tprev, pe);
-  T s0 = 0, s1 = 0, s2 = 0;
+  // t at the position at plane kk from the carried own ex, ey and the seven
+  // other E values of curlE (all NB right-hand sides loaded first); own ez
+  // and the plane kk+1 ex, ey are returned for the caller.
+  auto tplane = [&](int kk, cplx<T> (*tk)[3], cplx<T> *oez, cplx<T> *nex, cplx<T> *ney, const T *mu,
+                    const T *sgm) {
+    const int64_t n = n00 + kk * sz;
+    const bool kp = kk + 1 < g.nz;
+    const T rz = g.rd(2, kk);
+    cplx<T> ez[NB], eyi[NB], ezi[NB], exj[NB], ezj[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const cplx<T> *pb = p + (int64_t)(b0 + (act[r] ? r : 0)) * stride;
+      const bool ok = act[r];
+      ez[r] = ok ? pb[2 * nc + n] : cplx<T>();
+      eyi[r] = ok && ip ? pb[nc + n + 1] : cplx<T>();
+      ezi[r] = ok && ip ? pb[2 * nc + n + 1] : cplx<T>();
+      exj[r] = ok && jp ? pb[n + sy] : cplx<T>();
+      ezj[r] = ok && jp ? pb[2 * nc + n + sy] : cplx<T>();
+      nex[r] = ok && kp ? pb[n + sz] : cplx<T>();
+      ney[r] = ok && kp ? pb[nc + n + sz] : cplx<T>();
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      cplx<T> ce[3];
+      ce[0] = ry * (ezj[r] - ez[r]) - rz * (ney[r] - cey[r]);
+      ce[1] = rz * (nex[r] - cex[r]) - rx * (ezi[r] - ez[r]);
+      ce[2] = rx * (eyi[r] - cey[r]) - ry * (exj[r] - cex[r]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cplx<T> o;
+        if (mu[c] != T(0)) o = cdiv(ce[c], (mu[c] * a.inv_dt) * zm1[r] + (T(0.5) * sgm[c]) * zp1[r]);
+        tk[r][c] = o;
+      }
+      oez[r] = ez[r];
+    }
+  };
+#pragma unroll
+  for (int r = 0; r < NB; ++r) { tpx[r] = cplx<T>(); tpy[r] = cplx<T>(); cex[r] = cplx<T>(); cey[r] = cplx<T>(); }
+  if (p1) load_carry(k0 > 0 ? k0 - 1 : k0);
+  if (p1 && k0 > 0) {
+    // t(k0-1) at the position (owners keep its x, y components); the carry
+    // moves to plane k0
+    const int64_t e = n00 + (int64_t)(k0 - 1) * sz;
+    T mu[3], sgm[3];
+    for (int c = 0; c < 3; ++c) { mu[c] = a.mu[c * nc + e]; sgm[c] = a.sgm[c * nc + e]; }
+    cplx<T> tk[NB][3], oez[NB], nex[NB], ney[NB];
+    tplane(k0 - 1, tk, oez, nex, ney, mu, sgm);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) { tpx[r] = tk[r][0]; tpy[r] = tk[r][1]; cex[r] = nex[r]; cey[r] = ney[r]; }
+  }
+  T s0[NB], s1[NB], s2[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) s0[r] = s1[r] = s2[r] = T(0);
   for (int kk = k0; kk < k1; ++kk) {
     const int par = kk & 1;
+    const int64_t e = n00 + (int64_t)kk * sz;
+    // material properties of both phases first
+    T mu[3] = {0, 0, 0}, sgm[3] = {0, 0, 0}, ep[3] = {0, 0, 0}, sg[3] = {0, 0, 0};
+    if (p1)
+      for (int c = 0; c < 3; ++c) { mu[c] = a.mu[c * nc + e]; sgm[c] = a.sgm[c * nc + e]; }
+    if (own)
+      for (int c = 0; c < 3; ++c) { ep[c] = a.eps[c * nc + e]; sg[c] = a.sig[c * nc + e]; }
+    cplx<T> tk[NB][3], pe[NB][3];
     if (p1) {
-      tcomp(pi, pj, kk, tk, pe);
+      cplx<T> oez[NB], nex[NB], ney[NB];
+      tplane(kk, tk, oez, nex, ney, mu, sgm);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        pe[r][0] = cex[r]; pe[r][1] = cey[r]; pe[r][2] = oez[r];
+        cex[r] = nex[r]; cey[r] = ney[r];
+      }
     } else {
-      tk[0] = tk[1] = tk[2] = cplx<T>();
+#pragma unroll
+      for (int r = 0; r < NB; ++r) tk[r][0] = tk[r][1] = tk[r][2] = pe[r][0] = pe[r][1] = pe[r][2] = cplx<T>();
     }
-    if (warp <= kSY || lane <= kSY)
-      for (int c = 0; c < 3; ++c) ts[par][c][prow][pcol] = tk[c];
+    if (writer)
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        for (int c = 0; c < 3; ++c) TS(par, r, c, prow, pcol) = tk[r][c];
     __syncthreads();
     if (own) {
-      const int i = pi, j = pj, r = prow, cl = pcol;
-      const int64_t n = g.id(i, j, kk);
-      const cplx<T> hx = ts[par][0][r][cl], hy = ts[par][1][r][cl], hz = ts[par][2][r][cl];
-      const cplx<T> hz_jm = ts[par][2][r - 1][cl], hx_jm = ts[par][0][r - 1][cl];
-      const cplx<T> hz_im = ts[par][2][r][cl - 1], hy_im = ts[par][1][r][cl - 1];
-      const cplx<T> hy_km = kk > 0 ? tprev[1] : cplx<T>(), hx_km = kk > 0 ? tprev[0] : cplx<T>();
-      const T rx = g.rdd(0, i), ry = g.rdd(1, j), rz = g.rdd(2, kk);
-      cplx<T> ch[3];
-      ch[0] = ry * (hz - hz_jm) - rz * (hy - hy_km);
-      ch[1] = rz * (hx - hx_km) - rx * (hz - hz_im);
-      ch[2] = rx * (hy - hy_im) - ry * (hx - hx_jm);
-      for (int c = 0; c < 3; ++c) {
-        const int64_t e = c * nc + n;
-        const T ep = a.eps[e];
-        cplx<T> out;
-        if (ep != T(0)) {
-          const cplx<T> a11 = (ep * a.inv_dt) * zm1 + (T(0.5) * a.sig[e]) * zp1;
-          out = a11 * pe[c] + a.cz[b] * ch[c];
-          if (VDOT) {
-            const cplx<T> w = edge_volume(a, c, i, j, kk) * (pe[c] * out);
-            s0 += w.re;
-            s1 += w.im;
+      const T rz = g.rdd(2, kk);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        if (!act[r]) continue;
+        const cplx<T> hx = tk[r][0], hy = tk[r][1], hz = tk[r][2];
+        const cplx<T> hz_jm = TS(par, r, 2, prow - 1, pcol), hx_jm = TS(par, r, 0, prow - 1, pcol);
+        const cplx<T> hz_im = TS(par, r, 2, prow, pcol - 1), hy_im = TS(par, r, 1, prow, pcol - 1);
+        const cplx<T> hy_km = kk > 0 ? tpy[r] : cplx<T>(), hx_km = kk > 0 ? tpx[r] : cplx<T>();
+        cplx<T> ch[3];
+        ch[0] = rdy * (hz - hz_jm) - rz * (hy - hy_km);
+        ch[1] = rz * (hx - hx_km) - rdx * (hz - hz_im);
+        ch[2] = rdx * (hy - hy_im) - rdy * (hx - hx_jm);
+        const cplx<T> czb = a.cz[b0 + r];
+        for (int c = 0; c < 3; ++c) {
+          cplx<T> out;
+          if (ep[c] != T(0)) {
+            const cplx<T> a11 = (ep[c] * a.inv_dt) * zm1[r] + (T(0.5) * sg[c]) * zp1[r];
+            out = a11 * pe[r][c] + czb * ch[c];
+            if (VDOT) {
+              const cplx<T> w = edge_volume(a, c, pi, pj, kk) * (pe[r][c] * out);
+              s0[r] += w.re;
+              s1[r] += w.im;
+            }
+            s2[r] += norm2(out);
           }
-          s2 += norm2(out);
+          q[(int64_t)(b0 + r) * stride + c * nc + e] = out;
         }
-        q[b * stride + e] = out;
+        tpx[r] = hx; tpy[r] = hy;
       }
-      tprev[0] = tk[0]; tprev[1] = tk[1]; tprev[2] = tk[2];
     }
   }
-  (void)sy; (void)sz;
   if (VDOT) {
-    double acc[3] = {(double)s0, (double)s1, (double)s2};
-    block_sum(acc, 3, sh);
     const int nparts = gridDim.y * gridDim.z;
     const int part = blockIdx.y + gridDim.y * blockIdx.z;
-    if (threadIdx.x == 0) {
-      double *pp = partials + ((size_t)b * nparts + part) * 3;
-      pp[0] = acc[0]; pp[1] = acc[1]; pp[2] = acc[2];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      if (!act[r]) continue;  // uniform across the CTA
+      double acc[3] = {(double)s0[r], (double)s1[r], (double)s2[r]};
+      block_sum(acc, 3, sh);
+      if (threadIdx.x == 0) {
+        double *pp = partials + ((size_t)(b0 + r) * nparts + part) * 3;
+        pp[0] = acc[0]; pp[1] = acc[1]; pp[2] = acc[2];
+      }
+      if (tickets) last_block_scalars(b0 + r, partials, tickets, sc, SM_ALPHA, sh, nparts);
+      __syncthreads();
     }
-    if (tickets) last_block_scalars(b, partials, tickets, sc, SM_ALPHA, sh, nparts);
   }
 }
 
-// Launch shape of schur_fused_kernel: tiles of kSX x kSY and z chunks sized
-// for about four CTAs per SM over all right-hand sides.
-struct SchurShape {
-  int ntx, nty, zchunk, nchunk;
-};
-inline SchurShape schur_shape(const fdtd_grid *g, int nb) {
-  SchurShape sh;
-  sh.ntx = (g->nx + kSX - 1) / kSX;
-  sh.nty = (g->ny + kSY - 1) / kSY;
-  const int64_t per = (int64_t)sh.ntx * sh.nty * nb;
+// Launch of schur_fused_kernel: tiles of kSX x kSY, right-hand sides in
+// groups of NB (3 for FP32: one per expansion point of L = 2; 1 for FP64),
+// z chunks sized for about four CTAs per SM.
+template <typename T, bool VDOT>
+fdtd_status launch_schur_fused(const fdtd_grid *g, const OpArgs<T> &a, int nb, const cplx<T> *p, cplx<T> *q,
+                               int64_t stride, CgsScal *sc, double *partials, unsigned *tickets, cudaStream_t s) {
+  // NB = 3 for the plain apply (0.80 against 1.00 ms on 384x384x64 with three
+  // right-hand sides); the COCG form keeps NB = 1, whose registers fit without
+  // spilling beside the dot-product terms
+  const char *env = getenv("FDTDMOR_SCHUR_NB");
+  int NB = (sizeof(T) == 8 || VDOT) ? 1 : std::min(nb, 3);
+  if (env && sizeof(T) == 4) NB = std::max(1, std::min(3, atoi(env)));
+  const int ntx = (g->nx + kSX - 1) / kSX, nty = (g->ny + kSY - 1) / kSY;
+  const int ngrp = (nb + NB - 1) / NB;
+  const int64_t per = (int64_t)ntx * nty * ngrp;
   int want = (int)std::max<int64_t>(1, (152 * 4 + per - 1) / per);
   want = std::min(want, std::max(1, g->nz / 4));
-  sh.zchunk = (g->nz + want - 1) / want;
-  sh.nchunk = (g->nz + sh.zchunk - 1) / sh.zchunk;
-  return sh;
+  const int zchunk = (g->nz + want - 1) / want;
+  const int nchunk = (g->nz + zchunk - 1) / zchunk;
+  const dim3 grid(ngrp, ntx * nty, nchunk);
+  const size_t smem = sizeof(cplx<T>) * 2 * NB * 3 * (kSY + 1) * (kSX + 1);
+  auto go = [&](auto kern) -> fdtd_status {
+    if (smem > 48 * 1024)
+      FDTD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kSThreads, smem, s>>>(a, nb, p, q, stride, ntx, zchunk, sc, partials, tickets);
+    return after_launch("schur_fused_kernel");
+  };
+  if (NB == 1) return go(schur_fused_kernel<T, VDOT, 1>);
+  if (NB == 2) return go(schur_fused_kernel<T, VDOT, 2>);
+  return go(schur_fused_kernel<T, VDOT, 3>);
 }
 
 // Jacobi preconditioner: P = 1 / diag(S(z)) on live E edges, 0 on dead ones.
@@ -770,7 +874,7 @@ __global__ void __launch_bounds__(MB) resid64_h_kernel(OpArgs<T> a, const cplx<d
 template <typename T>
 __global__ void __launch_bounds__(MB) resid64_e_kernel(OpArgs<T> a, const cplx<double> *__restrict__ t,
                                                        const cplx<double> *__restrict__ x, int64_t stride,
-                                                       const cplx<T> *__restrict__ bhat, cplx<T> *__restrict__ rout,
+                                                       const cplx<double> *__restrict__ bhat, cplx<T> *__restrict__ rout,
                                                        double *__restrict__ partials) {
   __shared__ double sh[3 * 32];
   const int b = blockIdx.y;
@@ -791,8 +895,7 @@ __global__ void __launch_bounds__(MB) resid64_e_kernel(OpArgs<T> a, const cplx<d
       cplx<double> rv;
       if (ep != 0.0) {
         const cplx<double> a11 = (ep * (double)a.inv_dt) * zm1 + (0.5 * (double)a.sig[e]) * zp1;
-        const cplx<T> bh = bhat[o];
-        rv = cplx<double>((double)bh.re, (double)bh.im) - (a11 * x[o] + z * ch[c]);
+        rv = bhat[o] - (a11 * x[o] + z * ch[c]);
       }
       rout[o] = cplx<T>((T)rv.re, (T)rv.im);
       acc[2] += norm2(rv);
@@ -802,6 +905,122 @@ __global__ void __launch_bounds__(MB) resid64_e_kernel(OpArgs<T> a, const cplx<d
   if (threadIdx.x == 0) {
     double *pb = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
     pb[0] = 0; pb[1] = 0; pb[2] = acc[2];
+  }
+}
+
+// Right-hand side of the Schur system in FP64 from a chain vector v of the
+// field type (or from B in r_in when v is null): r = (R+F) v, then
+// bhat = r1 + curlH(r2 / a22).  The curls of v and of r2 / a22 difference
+// neighbouring values of vectors whose near-static gradient part dominates;
+// in FP32 that cancellation leaves errors far above the solve tolerance in
+// the chain, so these steps run in FP64 like the residual.
+template <typename T>
+__global__ void __launch_bounds__(MB) rhs64_h_kernel(OpArgs<T> a, const cplx<T> *__restrict__ v, int64_t vstride,
+                                                     cplx<double> *__restrict__ r2, cplx<double> *__restrict__ t,
+                                                     int64_t stride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+  const cplx<double> z((double)a.z[b].re, (double)a.z[b].im), zm1(z.re - 1.0, z.im), zp1(z.re + 1.0, z.im);
+  cplx<double> ce[3];
+  const cplx<T> *vb = v ? v + b * vstride : nullptr;
+  if (vb) {
+    auto ld = [&](int64_t idx) { const cplx<T> x = vb[idx]; return cplx<double>((double)x.re, (double)x.im); };
+    curl_e3<T, cplx<double>>(a.g, ld, i, j, k, n, ce);
+  }
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const double mu = (double)a.mu[e];
+    cplx<double> rv, tv;
+    if (mu != 0.0 && vb) {
+      const cplx<T> h = vb[3 * nc + e];
+      rv = ce[c] + (mu * (double)a.inv_dt + 0.5 * (double)a.sgm[e]) * cplx<double>((double)h.re, (double)h.im);
+      tv = cdiv(rv, (mu * (double)a.inv_dt) * zm1 + (0.5 * (double)a.sgm[e]) * zp1);
+    }
+    r2[b * stride + e] = rv;
+    t[b * stride + e] = tv;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MB) rhs64_e_kernel(OpArgs<T> a, const cplx<T> *__restrict__ v, int64_t vstride,
+                                                     const cplx<double> *__restrict__ t,
+                                                     cplx<double> *__restrict__ bhat, int64_t stride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+  const cplx<double> *tb = t + b * stride;
+  auto ld = [&](int64_t idx) { return tb[idx]; };
+  cplx<double> ch[3];
+  curl_h3<T, cplx<double>>(a.g, ld, i, j, k, n, ch);
+  const cplx<T> *vb = v + b * vstride;
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const double ep = (double)a.eps[e];
+    cplx<double> out;
+    if (ep != 0.0) {
+      const cplx<T> x = vb[e];
+      out = (ep * (double)a.inv_dt + 0.5 * (double)a.sig[e]) * cplx<double>((double)x.re, (double)x.im) + ch[c];
+    }
+    bhat[b * stride + e] = out;
+  }
+}
+
+// bhat (FP64) = B in r_in's E part (the chain's first right-hand side)
+template <typename T>
+__global__ void rhs64_b_kernel(OpArgs<T> a, const cplx<T> *__restrict__ rin, int64_t rstride,
+                               cplx<double> *__restrict__ bhat, cplx<double> *__restrict__ r2, int64_t stride) {
+  const int b = blockIdx.y;
+  const int64_t n3 = 3 * a.g.nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
+    const cplx<T> x = rin[b * rstride + e];
+    bhat[b * stride + e] = a.eps[e] != T(0) ? cplx<double>((double)x.re, (double)x.im) : cplx<double>();
+    r2[b * stride + e] = cplx<double>();
+  }
+}
+
+// out = [x1; x2] from the FP64 solution: x1 = x, x2 = (r2 - z curlE(x1)) / a22
+// in FP64, both rounded to the field type
+template <typename T>
+__global__ void __launch_bounds__(MB) recover64_kernel(OpArgs<T> a, const cplx<double> *__restrict__ x,
+                                                       const cplx<double> *__restrict__ r2, int64_t stride,
+                                                       cplx<T> *__restrict__ out, int64_t ostride) {
+  const int b = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = a.g.nc;
+  if (n >= nc) return;
+  int i, j, k;
+  cell_ijk(n, a.g.nx, a.g.ny, nc, i, j, k);
+  const cplx<double> *xb = x + b * stride;
+  auto ld = [&](int64_t idx) { return xb[idx]; };
+  const cplx<double> z((double)a.z[b].re, (double)a.z[b].im), zm1(z.re - 1.0, z.im), zp1(z.re + 1.0, z.im);
+  cplx<double> ce[3];
+  curl_e3<T, cplx<double>>(a.g, ld, i, j, k, n, ce);
+  cplx<T> *ob = out + b * ostride;
+  for (int c = 0; c < 3; ++c) {
+    const int64_t e = c * nc + n;
+    const cplx<double> x1 = xb[e];
+    ob[e] = cplx<T>((T)x1.re, (T)x1.im);
+    const double mu = (double)a.mu[e];
+    cplx<double> x2;
+    if (mu != 0.0) x2 = cdiv(r2[b * stride + e] - z * ce[c], (mu * (double)a.inv_dt) * zm1 + (0.5 * (double)a.sgm[e]) * zp1);
+    ob[3 * nc + e] = cplx<T>((T)x2.re, (T)x2.im);
+  }
+}
+
+// FP64 copy of an E block of the field type
+template <typename T>
+__global__ void to64_kernel(int64_t len, const cplx<T> *__restrict__ x, cplx<double> *__restrict__ y, int64_t stride) {
+  const int b = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const cplx<T> v = x[b * stride + e];
+    y[b * stride + e] = cplx<double>((double)v.re, (double)v.im);
   }
 }
 
@@ -1097,6 +1316,7 @@ struct Work {
   DevBuf phi, dN;  // nb x nc nodal potential and nodal diagonal (COCG)
   DevBuf upd;      // nb ints: right-hand sides the last inner solve updated
   DevBuf tickets;  // 2 x kMaxRhs CTA tickets of the fused scalar updates (COCG)
+  DevBuf bhat64, r2_64;  // nb x 3nc complex FP64: right-hand side and H part of (R+F) v (COCG)
 };
 
 template <typename T>
@@ -1180,9 +1400,53 @@ struct BasisBuilder {
   // written to out, nb x 6nc).  v: nb x 6nc (B itself when from_b).
   fdtd_status solve(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b,
                     const cplx<T> *vin, cplx<T> *out) {
+    if (uses_cocg()) {
+      FDTD_CHECK(make_rhs64(w, zs, from_b, vin));
+      FDTD_CHECK(schur_cocg(w, zs));
+      return recover64(w, zs, out);
+    }
     FDTD_CHECK(make_rhs(w, zs, from_b, vin));
     FDTD_CHECK(schur_solve(w, zs));
     return recover(w, zs, out);
+  }
+
+  bool uses_cocg() const {
+    return o.solver == MOR_SOLVER_COCG || (o.solver == MOR_SOLVER_AUTO && g->prec != FDTD_F64);
+  }
+
+  fdtd_status alloc64(Work<T> &w, int nb) {
+    const size_t n = sizeof(cplx<double>) * nb * 3 * nc;
+    FDTD_CHECK(w.bhat64.alloc(n, s));
+    FDTD_CHECK(w.r2_64.alloc(n, s));
+    FDTD_CHECK(w.x64.alloc(n, s));
+    return w.t64.alloc(n, s);
+  }
+
+  // FP64 bhat (and r2 for the recovery) from the chain vector or from B
+  fdtd_status make_rhs64(Work<T> &w, const std::vector<std::complex<double>> &zs, bool from_b, const cplx<T> *vin) {
+    const int nb = (int)zs.size();
+    const int64_t n3 = 3 * nc, n6 = 6 * nc;
+    std::vector<std::complex<double>> one(nb, 1.0);
+    FDTD_CHECK(alloc64(w, nb));
+    OpArgs<T> a = make_op<T>(g, o.dt0, zs, one);
+    cplx<double> *bh = w.bhat64.template as<cplx<double>>(), *r2 = w.r2_64.template as<cplx<double>>();
+    cplx<double> *t = w.t64.template as<cplx<double>>();
+    if (from_b) {
+      rhs64_b_kernel<T><<<dim3(std::min(nblk, 152 * 8), nb), MB, 0, s>>>(a, w.r.template as<cplx<T>>(), n6, bh, r2, n3);
+      return after_launch("rhs64_b_kernel");
+    }
+    rhs64_h_kernel<T><<<dim3(nblk, nb), MB, 0, s>>>(a, vin, n6, r2, t, n3);
+    FDTD_CHECK(after_launch("rhs64_h_kernel"));
+    rhs64_e_kernel<T><<<dim3(nblk, nb), MB, 0, s>>>(a, vin, n6, t, bh, n3);
+    return after_launch("rhs64_e_kernel");
+  }
+
+  fdtd_status recover64(Work<T> &w, const std::vector<std::complex<double>> &zs, cplx<T> *out) {
+    const int nb = (int)zs.size();
+    OpArgs<T> a = make_op<T>(g, o.dt0, zs, zs);
+    recover64_kernel<T><<<dim3(nblk, nb), MB, 0, s>>>(a, w.x64.template as<cplx<double>>(),
+                                                      w.r2_64.template as<cplx<double>>(), 3 * nc, out, 6 * nc);
+    return after_launch("recover64_kernel");
   }
 
   // bhat = r1 + curlH(r2 / a22) of r = (R+F) v (or of r = B already in w.r)
@@ -1223,8 +1487,15 @@ struct BasisBuilder {
   // grids); the paper's CGS (AUTO on FP64 grids, falling back to BiCGSTAB for
   // the whole block when a right-hand side fails); or BiCGSTAB.
   fdtd_status schur_solve(Work<T> &w, const std::vector<std::complex<double>> &zs) {
-    if (o.solver == MOR_SOLVER_COCG || (o.solver == MOR_SOLVER_AUTO && g->prec != FDTD_F64))
+    if (uses_cocg()) {
+      // bhat of the field type (mor_shifted_solve) -> FP64
+      const int nb = (int)zs.size();
+      FDTD_CHECK(alloc64(w, nb));
+      to64_kernel<T><<<dim3(std::min(nblk, 152 * 8), nb), MB, 0, s>>>(3 * nc, w.bhat.template as<cplx<T>>(),
+                                                                       w.bhat64.template as<cplx<double>>(), 3 * nc);
+      FDTD_CHECK(after_launch("to64_kernel"));
       return schur_cocg(w, zs);
+    }
     if (o.solver != MOR_SOLVER_AUTO) return schur_krylov(w, zs, o.solver);
     const bool nc0 = noconv;
     const int it0 = max_iters;
@@ -1253,9 +1524,8 @@ struct BasisBuilder {
     dim3 grid2(nblk, nb);
     OpArgs<T> ap = make_op<T>(g, o.dt0, zs, zz);    // e_from_h half: cz = z
     OpArgs<T> ah1 = make_op<T>(g, o.dt0, zs, one);  // h_from_e half: cz = 1
-    cplx<T> *t = w.t.template as<cplx<T>>(), *bh = w.bhat.template as<cplx<T>>();
-    FDTD_CHECK(w.x64.alloc(sizeof(cplx<double>) * nb * n3, s));
-    FDTD_CHECK(w.t64.alloc(sizeof(cplx<double>) * nb * n3, s));
+    cplx<T> *t = w.t.template as<cplx<T>>();
+    const cplx<double> *bh = w.bhat64.template as<cplx<double>>();
     FDTD_CHECK(w.phi.alloc(sizeof(cplx<T>) * nb * nc, s));
     FDTD_CHECK(w.dN.alloc(sizeof(cplx<T>) * nb * nc, s));
     FDTD_CHECK(w.upd.alloc(sizeof(int) * kMaxRhs, s));
@@ -1287,15 +1557,12 @@ struct BasisBuilder {
     // one-pass Schur apply (FDTDMOR_SCHUR=pair selects the two-kernel form)
     const char *sch = getenv("FDTDMOR_SCHUR");
     const bool fused = !(sch && std::string(sch) == "pair");
-    const SchurShape shp = schur_shape(g, nb);
     const int *act = reinterpret_cast<const int *>(reinterpret_cast<const char *>(sc) + offsetof(CgsScal, active));
     auto iteration = [&](cudaStream_t st) -> fdtd_status {
       cocg_update_p_kernel<T><<<gridE, MB, 0, st>>>(n3, sc, zv, p, n3);
       FDTD_CHECK(after_launch("cocg_update_p_kernel"));
       if (fused) {
-        schur_fused_kernel<T, true><<<dim3(nb, shp.ntx * shp.nty, shp.nchunk), kSThreads, 0, st>>>(
-            ap, p, q, n3, shp.ntx, shp.zchunk, sc, part, tk);
-        FDTD_CHECK(after_launch("schur_fused_kernel"));
+        FDTD_CHECK((launch_schur_fused<T, true>(g, ap, nb, p, q, n3, sc, part, tk, st)));
       } else {
         h_from_e_kernel<T><<<grid2, MB, 0, st>>>(ah1, p, n3, nullptr, 0, nullptr, 0, t, n3, act, astride);
         FDTD_CHECK(after_launch("h_from_e_kernel"));
@@ -1654,7 +1921,7 @@ static fdtd_status shifted_solve_t(fdtd_grid *g, const mor_opts &o, const std::v
     ~Rel() {
       cudaStreamSynchronize(s);
       for (DevBuf *d : {&w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc,
-                        &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets})
+                        &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets, &w.bhat64, &w.r2_64})
         d->release(s);
     }
   } rel{w, s};
@@ -1909,7 +2176,8 @@ static fdtd_status build_basis_t(fdtd_grid *g, const mor_opts &o, cudaStream_t s
   }
   FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
   for (DevBuf *d : {&w.v, &w.r, &w.bhat, &w.P, &w.x, &w.rr, &w.rt, &w.u, &w.p, &w.q, &w.vv, &w.t, &w.partials, &w.sc,
-                    &w.dots, &w.dpart, &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets, &chains, &xs, &tmp})
+                    &w.dots, &w.dpart, &w.x64, &w.t64, &w.phi, &w.dN, &w.upd, &w.tickets, &w.bhat64, &w.r2_64,
+                    &chains, &xs, &tmp})
     d->release(s);
   B->max_iters = bb.max_iters;
   B->max_resid = bb.max_resid;
@@ -2010,12 +2278,8 @@ fdtd_status mor_schur_apply(fdtd_grid *g, double dt0, int nb, const double *z, c
     using T = decltype(tag);
     const OpArgs<T> ah1 = make_op<T>(g, dt0, zs, one), ap = make_op<T>(g, dt0, zs, zs);
     const cplx<T> *xv = static_cast<const cplx<T> *>(x);
-    if (!pair) {
-      const SchurShape shp = schur_shape(g, nb);
-      schur_fused_kernel<T, false><<<dim3(nb, shp.ntx * shp.nty, shp.nchunk), kSThreads, 0, s>>>(
-          ap, xv, static_cast<cplx<T> *>(y), n3, shp.ntx, shp.zchunk, nullptr, nullptr, nullptr);
-      return after_launch("schur_fused_kernel");
-    }
+    if (!pair)
+      return launch_schur_fused<T, false>(g, ap, nb, xv, static_cast<cplx<T> *>(y), n3, nullptr, nullptr, nullptr, s);
     DevBuf t;
     FDTD_CHECK(t.alloc((size_t)nb * n3 * sizeof(cplx<T>), s));
     h_from_e_kernel<T><<<grid2, MB, 0, s>>>(ah1, xv, n3, nullptr, 0, nullptr, 0, t.as<cplx<T>>(), n3, nullptr);

@@ -5,10 +5,18 @@
 //   e <- Pe e - Qe h + be u^{n+1}
 //   h <- Ph h + Qh e + bh u^{n+1}
 //   y^n = C~ e
-// The two phases depend on each other, so one CTA of 1024 threads runs all
-// steps with a block barrier between phases; the step matrices sit in shared
-// memory when they fit (q up to about 90 in FP32), else they stream from L2.
+// The two phases depend on each other.  When the step matrices fit one CTA's
+// shared memory (q up to about 90 in FP32) one CTA of 1024 threads runs all
+// steps with a block barrier between phases.  Larger models run on a thread
+// block cluster whose CTAs each hold a slice of rows of the step matrices in
+// shared memory (resident for the whole run); each phase's new state slice is
+// stored into every CTA's copy of the state through distributed shared
+// memory, with one cluster barrier per phase.  Models too large for 16 CTAs
+// stream the matrices from L2 in the one-CTA kernel.
 #include <algorithm>
+#include <cooperative_groups.h>
+#include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "mor_common.cuh"
@@ -88,6 +96,94 @@ __global__ void __launch_bounds__(1024) reduced_run_kernel(RunArgs<T> a) {
   for (int t = threadIdx.x; t < q1 + q2; t += blockDim.x) a.state[t] = sm[t];
 }
 
+// Cluster form.  CTA `rank` of the cluster owns rows [rank*er, rank*er + er)
+// of e and [rank*hr, ...) of h, with those rows of Pe, Qe, be and of Ph, Qh,
+// bh in its shared memory, and a double-buffered copy of the whole state
+// (slot n & 1 is read in step n, slot (n+1) & 1 written).  Per step: phase E
+// computes its rows of e^{n+1} and stores them into slot (n+1)&1 of every
+// CTA (DSMEM); cluster barrier; phase H computes its rows of h^{n+1} from
+// e^{n+1} likewise and rank 0 forms y^n = C~ e^{n+1}; cluster barrier.  A
+// slot is rewritten only two barriers after its last read, so the two
+// barriers per step are all the ordering the exchange needs.
+constexpr int kRunClusterThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kRunClusterThreads) reduced_run_cluster_kernel(RunArgs<T> a, int er, int hr) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), ncta = (int)cluster.num_blocks();
+  const int q1 = a.q1, q2 = a.q2, m = a.m, p = a.p;
+  const int e0 = rank * er, ne = max(0, min(q1, e0 + er) - e0);
+  const int h0 = rank * hr, nh = max(0, min(q2, h0 + hr) - h0);
+  const int mp = (m + 1) & ~1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *E = reinterpret_cast<T *>(smraw);  // [2][q1]
+  T *H = E + 2 * q1;                     // [2][q2]
+  T *us = H + 2 * q2;                    // [mp]
+  T *Pe = us + mp, *Qe = Pe + (size_t)er * q1, *be = Qe + (size_t)er * q2;
+  T *Ph = be + (size_t)er * m, *Qh = Ph + (size_t)hr * q2, *bh = Qh + (size_t)hr * q1, *C = bh + (size_t)hr * m;
+  for (int t = threadIdx.x; t < ne * q1; t += blockDim.x) Pe[t] = a.Pe[(size_t)e0 * q1 + t];
+  for (int t = threadIdx.x; t < ne * q2; t += blockDim.x) Qe[t] = a.Qe[(size_t)e0 * q2 + t];
+  for (int t = threadIdx.x; t < ne * m; t += blockDim.x) be[t] = a.be[(size_t)e0 * m + t];
+  for (int t = threadIdx.x; t < nh * q2; t += blockDim.x) Ph[t] = a.Ph[(size_t)h0 * q2 + t];
+  for (int t = threadIdx.x; t < nh * q1; t += blockDim.x) Qh[t] = a.Qh[(size_t)h0 * q1 + t];
+  for (int t = threadIdx.x; t < nh * m; t += blockDim.x) bh[t] = a.bh[(size_t)h0 * m + t];
+  if (rank == 0)
+    for (int t = threadIdx.x; t < p * q1; t += blockDim.x) C[t] = a.C[t];
+  for (int t = threadIdx.x; t < q1; t += blockDim.x) E[t] = a.state[t];
+  for (int t = threadIdx.x; t < q2; t += blockDim.x) H[t] = a.state[q1 + t];
+  cluster.sync();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t n = 0; n < a.nsteps; ++n) {
+    const int cur = (int)(n & 1), nxt = cur ^ 1;
+    const T *e = E + cur * q1, *h = H + cur * q2;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) us[t] = a.u[n * m + t];
+    __syncthreads();
+    for (int r = w; r < ne; r += nw) {
+      T acc = 0;
+      for (int c = lane; c < q1; c += 32) acc += Pe[r * q1 + c] * e[c];
+      for (int c = lane; c < q2; c += 32) acc -= Qe[r * q2 + c] * h[c];
+      for (int c = lane; c < m; c += 32) acc += be[r * m + c] * us[c];
+      acc = warp_sum(acc);
+      for (int d = lane; d < ncta; d += 32) cluster.map_shared_rank(E, d)[nxt * q1 + e0 + r] = acc;
+    }
+    cluster.sync();
+    const T *en = E + nxt * q1;
+    for (int r = w; r < nh; r += nw) {
+      T acc = 0;
+      for (int c = lane; c < q2; c += 32) acc += Ph[r * q2 + c] * h[c];
+      for (int c = lane; c < q1; c += 32) acc += Qh[r * q1 + c] * en[c];
+      for (int c = lane; c < m; c += 32) acc += bh[r * m + c] * us[c];
+      acc = warp_sum(acc);
+      for (int d = lane; d < ncta; d += 32) cluster.map_shared_rank(H, d)[nxt * q2 + h0 + r] = acc;
+    }
+    if (rank == 0)
+      for (int r = w; r < p; r += nw) {
+        T acc = 0;
+        for (int c = lane; c < q1; c += 32) acc += C[r * q1 + c] * en[c];
+        acc = warp_sum(acc);
+        if (lane == 0) a.y[n * p + r] = acc;
+      }
+    cluster.sync();
+  }
+  if (rank == 0) {
+    const int fin = (int)(a.nsteps & 1);
+    for (int t = threadIdx.x; t < q1; t += blockDim.x) a.state[t] = E[fin * q1 + t];
+    for (int t = threadIdx.x; t < q2; t += blockDim.x) a.state[q1 + t] = H[fin * q2 + t];
+  }
+}
+
+// Shared memory of the cluster form with cl CTAs (row slices er, hr); 0 if
+// it exceeds 200 KB per CTA.
+template <typename T>
+static size_t run_cluster_smem(int cl, int q1, int q2, int m, int p, int &er, int &hr) {
+  er = (q1 + cl - 1) / cl;
+  hr = (q2 + cl - 1) / cl;
+  const size_t smem = sizeof(T) * (2 * (size_t)(q1 + q2) + ((m + 1) & ~1) + (size_t)er * (q1 + q2 + m) +
+                                   (size_t)hr * (q2 + q1 + m) + (size_t)p * q1);
+  return smem <= 200 * 1024 ? smem : 0;
+}
+
 template <typename T>
 static fdtd_status run_t(mor_model *M, int64_t nsteps, const void *u, void *y, int reset, cudaStream_t s) {
   const int q1 = M->q1, q2 = M->q2, m = M->m, p = M->p;
@@ -105,6 +201,46 @@ static fdtd_status run_t(mor_model *M, int64_t nsteps, const void *u, void *y, i
   const size_t mats = sizeof(T) * ((size_t)q1 * q1 + 2 * (size_t)q1 * q2 + (size_t)q2 * q2 + (size_t)(q1 + q2) * m + (size_t)p * q1);
   const size_t limit = 220 * 1024;
   a.mats_in_smem = vec + mats <= limit;
+  // Cluster form when the matrices exceed one CTA (FDTDMOR_RUN=cta / cluster
+  // forces a form).  The largest schedulable cluster wins: measured at q = 200
+  // (FP32) 7.3, 4.4 and 3.3 us per step with 4, 8 and 16 CTAs (21.8 with one
+  // CTA streaming from L2); FDTDMOR_RUN_CL caps the size.
+  const char *env = getenv("FDTDMOR_RUN");
+  const std::string form = env ? env : "";
+  const char *envc = getenv("FDTDMOR_RUN_CL");
+  const int cl_max = envc ? std::max(2, std::min(16, atoi(envc))) : 16;
+  if ((!a.mats_in_smem && form != "cta") || form == "cluster") {
+    auto kern = reduced_run_cluster_kernel<T>;
+    for (int cl = cl_max; cl >= 2; cl /= 2) {
+      int er = 0, hr = 0;
+      const size_t csm = run_cluster_smem<T>(cl, q1, q2, m, p, er, hr);
+      if (csm == 0) break;  // smaller clusters need even more per CTA
+      FDTD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      if (cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(kRunClusterThreads);
+      cfg.dynamicSmemBytes = csm;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();  // not schedulable: try a smaller cluster
+        continue;
+      }
+      FDTD_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, a, er, hr));
+      return after_launch("reduced_run_cluster_kernel");
+    }
+  }
   const size_t smem = a.mats_in_smem ? vec + mats : vec;
   FDTD_REQUIRE(vec <= limit, "reduced order too large for the reduced-run kernel");
   FDTD_CHECK_CUDA(cudaFuncSetAttribute(reduced_run_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
