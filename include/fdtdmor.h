@@ -187,10 +187,30 @@ FDTD_API fdtd_status fdtd_step_host(fdtd_grid *grid, double dt, int64_t nsteps, 
 FDTD_API fdtd_status fdtd_step_batched(fdtd_grid *const *grids, int ngrids, const double *dt, int64_t nsteps,
                               const void *const *u, void *const *y, int reset_fields, fdtd_stream_t stream);
 
-/* Synchronise the stream and report FDTD_ETIMEOUT if a bounded device-side wait
- * of an earlier fdtd_step on this grid gave up (the flag is then cleared): an
- * mbarrier wait of the TMA form, or a grid barrier of the persistent form
- * (about one second each).  The fields are then undefined. */
+/* Field watchdog of fdtd_step / fdtd_step_host (on by default, NaN/Inf
+ * only): after each call the squares of the six field arrays are summed in
+ * FP64; a sum that is not finite -- a leap-frog run beyond its stability
+ * limit, Eq. (singular_limit), overflows -- sets the grid's flag, which
+ * fdtd_check reports as FDTD_EUNSTABLE.  growth > 0 also flags a source-free
+ * call (no sources, or u = NULL, fields not reset) whose sum grew by more than
+ * that factor (the discrete energy x^T R x of Eq. (R_and_F) cannot grow
+ * without sources).  sync != 0: fdtd_step synchronises its stream and returns
+ * FDTD_EUNSTABLE itself.  enable = 0 switches the watchdog off (one reduction
+ * over the fields per call saved). */
+FDTD_API fdtd_status fdtd_grid_set_watchdog(fdtd_grid *grid, int enable, double growth, int sync);
+
+/* Polls of a completion-counter wait of the dataflow stepping form
+ * (FDTD_KERNEL_PERSIST) before it gives up, sets the grid's flag and returns
+ * (fdtd_check then reports FDTD_ETIMEOUT; the fields are not valid).  polls < 0
+ * restores the default, 2^24 (about a second).  TMA pipeline waits keep their
+ * own fixed limits. */
+FDTD_API fdtd_status fdtd_grid_set_wait_limit(fdtd_grid *grid, long long polls);
+
+/* Synchronise the stream and report the grid's flag (then cleared):
+ * FDTD_ETIMEOUT if a bounded device-side wait of an earlier fdtd_step gave up
+ * (an mbarrier wait of a TMA-staged form, or a completion-counter wait of the
+ * dataflow form; the fields are then undefined), FDTD_EUNSTABLE if the field
+ * watchdog fired (fdtd_grid_set_watchdog). */
 FDTD_API fdtd_status fdtd_check(fdtd_grid *grid, fdtd_stream_t stream);
 
 /* Copy the six field arrays (Ex, Ey, Ez, Hx, Hy, Hz, each nx*ny*nz of the
@@ -282,8 +302,12 @@ typedef enum { MOR_ORTH_NATIVE = 0, MOR_ORTH_TF32 = 1, MOR_ORTH_BF16 = 2 } mor_o
  * arith: MOR_ORTH_NATIVE = FP32 CUDA-core products with FP64 sums every 256
  * rows (needs lda = ldb = n); MOR_ORTH_TF32 / MOR_ORTH_BF16 = tcgen05 tensor
  * cores with TF32 / BF16 inputs and FP32 accumulation over row chunks, the
- * chunk sums added in FP64.  M, N <= 65535.  Synchronises the stream;
- * FDTD_ETIMEOUT if a bounded pipeline wait gave up. */
+ * chunk sums added in FP64; MOR_GRAM_TF32X3 / MOR_GRAM_BF16X3 = the same in
+ * three passes over a head/remainder split of each operand
+ * (Ah^T Bh + Ah^T Bl + Al^T Bh), relative error O(2^-20) / O(2^-16) of
+ * |A||B| -- the products mor_project uses on the tensor cores.  M, N <= 65535.
+ * Synchronises the stream; FDTD_ETIMEOUT if a bounded pipeline wait gave up. */
+enum { MOR_GRAM_TF32X3 = 3, MOR_GRAM_BF16X3 = 4 };
 FDTD_API fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, const float *B, int64_t ldb,
                      int N, const float *w, double *G, fdtd_stream_t stream);
 
@@ -333,8 +357,10 @@ typedef struct {
 FDTD_API fdtd_status mor_shifted_solve(fdtd_grid *grid, const mor_opts *opts, int nb, const double *z,
                                        const void *b, void *x, int *iters, double *resid, fdtd_stream_t stream);
 
-/* Fill *opts with M = 1.1, L = 2, tol = 1e-4, maxit = 20000, defl_tol = 1e-8
- * (FP64) -- q, fmax and dt0 must still be set by the caller. */
+/* Fill *opts with M = 1.1, L = 2, tol = 1e-4, maxit = 20000, defl_tol = 1e-8,
+ * orth = MOR_ORTH_TF32 (tensor cores on FDTD_F32 grids: TF32 first CGS2 pass,
+ * split-precision projection; FDTD_F64 grids always use FP64 products),
+ * solver = AUTO -- q, fmax and dt0 must still be set by the caller. */
 FDTD_API fdtd_status mor_opts_default(mor_opts *opts);
 
 /* A3-A5 -- SPRIM basis (Sec. II-C, Sec. IV): for each expansion point
@@ -359,7 +385,10 @@ FDTD_API fdtd_status mor_basis_destroy(mor_basis *basis);
 
 /* A6 -- projection, Eq. (R_and_Freduced): D~eps = V1^T D_eps V1,
  * D~se = V1^T D_se V1, D~mu = V2^T D_mu V2, D~sm = V2^T D_sm V2,
- * K~ = V1^T K V2, B~ = V^T B, C~ = C V, accumulated in FP64. */
+ * K~ = V1^T K V2, B~ = V^T B, C~ = C V, accumulated in FP64.  For a basis
+ * built with MOR_ORTH_TF32 / MOR_ORTH_BF16 the five Gram products run on the
+ * tensor cores in split precision (MOR_GRAM_TF32X3 / MOR_GRAM_BF16X3); else
+ * on the CUDA cores in the grid's type. */
 FDTD_API fdtd_status mor_project(fdtd_grid *grid, const mor_basis *basis, fdtd_stream_t stream,
                                  mor_model **out);
 
@@ -411,10 +440,9 @@ FDTD_API fdtd_status mor_compare(const void *y_red, const void *y_ref, int64_t n
                                  fdtd_stream_t stream);
 
 /* The comparison of mor_compare without any device allocation, for callers
- * that cannot allocate while it runs: code inside a CUDA stream capture
- * (cudaMalloc cannot be captured), a host application or plugin that owns all
- * device memory itself, or a run under an allocator that must not grow.  The
- * paper has no counterpart; this is a deployment variant of the A9 step.
+ * that cannot allocate while it runs: a host application or plugin that owns
+ * all device memory itself, or a run under an allocator that must not grow.
+ * The paper has no counterpart; this is a deployment variant of the A9 step.
  * Arguments and result are those of mor_compare.  Its reduction scratch is a
  * static device array inside the library (64 KiB, held on every device that
  * loads the library until the process exits), so n * p is limited to

@@ -146,7 +146,12 @@ struct fdtd_grid {
   int64_t ctab_version = 0;     // bumped by every rebuild of ctab
   fdtdmor::DevBuf uflag;        // per (tile, plane) uniform material id or -1 (fast Yee kernel)
   bool uflag_ready = false;
-  fdtdmor::DevBuf errflag;      // set by kernels whose bounded device waits gave up
+  fdtdmor::DevBuf errflag;      // bit 2: a bounded device wait gave up; bits 4, 8: watchdog (NaN/Inf, growth)
+  int64_t wait_limit = (int64_t)1 << 24;  // polls of a dataflow-kernel counter wait before it gives up
+  bool wd_on = true;            // field watchdog after every fdtd_step call
+  double wd_growth = 0;         // > 0: flag source-free calls whose field energy grows by more than this factor
+  bool wd_sync = false;         // synchronise and return FDTD_EUNSTABLE from fdtd_step when flagged
+  fdtdmor::DevBuf wd_acc;       // 2 doubles: field energy before and after the call
   fdtdmor::DevBuf eprops;       // per-edge eps, sig (E) and mu, sgm (H), 4 x 3 x nc (reduction kernels)
   bool eprops_ready = false;
   cudaStream_t create_stream = nullptr;

@@ -207,12 +207,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const __grid_con
 }
 
 // out[m][n] = sum_z partial[z][m][n] in FP64, fixed order.
-__global__ void gram_tc_sum_kernel(int nsplit, int MN, const float *__restrict__ partial, double *__restrict__ out) {
+__global__ void gram_tc_sum_kernel(int nsplit, int MN, const float *__restrict__ partial, double *__restrict__ out,
+                                   int accumulate) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= MN) return;
   double a = 0;
   for (int z = 0; z < nsplit; ++z) a += (double)partial[(size_t)z * MN + t];
-  out[t] = a;
+  out[t] = accumulate ? out[t] + a : a;
+}
+
+// Split of an FP32 operand into a head in the tensor-core input type and the
+// remainder in the same type: v = hi + lo + O(2^-20 |v|) for TF32 (hi = v with
+// the 13 low mantissa bits cleared, which is what the TF32 MMA reads of an
+// FP32 value), O(2^-16 |v|) for BF16 (round to nearest twice).  Packed like
+// gram_pack_kernel: dst[c][r], (w ? w[r] : 1) applied first, zeros past n.
+template <typename D>
+__global__ void gram_split_kernel(int64_t n, int64_t n_pad, const float *__restrict__ src, int64_t ld,
+                                  const float *__restrict__ w, D *__restrict__ hi, D *__restrict__ lo) {
+  const int c = blockIdx.y;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_pad; r += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    if (r < n) {
+      v = src[(size_t)c * ld + r];
+      if (w) v *= w[r];
+    }
+    const size_t o = (size_t)c * n_pad + r;
+    if constexpr (sizeof(D) == 2) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[o] = h;
+      lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+      const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+      hi[o] = h;
+      lo[o] = v - h;
+    }
+  }
 }
 
 // dst[c][r] = (w ? w[r] : 1) src[c * ld + r] for r < n, 0 for n <= r < n_pad.
@@ -289,7 +318,8 @@ fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const
 // row stride lda, B likewise (strides x element size multiples of 16 bytes,
 // 16-byte-aligned bases).  part: scratch for the FP32 partials.
 fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void *A, int64_t lda, int M,
-                               const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part) {
+                               const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part,
+                               bool accumulate) {
   if (M == 0 || N == 0) return FDTD_OK;
   const int es = bf16 ? 2 : 4;
   FDTD_REQUIRE(M <= 65535 && N <= 65535, "gram_tensor: at most 65535 columns");
@@ -320,7 +350,7 @@ fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void 
                                                        err);
   FDTD_CHECK(after_launch("gram_tc_kernel"));
   const int MN = M * N;
-  gram_tc_sum_kernel<<<(MN + 255) / 256, 256, 0, s>>>(nsplit, MN, part.as<float>(), out);
+  gram_tc_sum_kernel<<<(MN + 255) / 256, 256, 0, s>>>(nsplit, MN, part.as<float>(), out, accumulate ? 1 : 0);
   return after_launch("gram_tc_sum_kernel");
 }
 
@@ -358,7 +388,44 @@ fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, in
     }
     lb = n_pad;
   }
-  return gram_tensor_kmajor(s, bf16, nk, pA, la, M, pB, lb, N, out, err, part);
+  return gram_tensor_kmajor(s, bf16, nk, pA, la, M, pB, lb, N, out, err, part, false);
+}
+
+// Split-precision G = A^T diag(w) B on the tensor cores: with A = Ah + Al and
+// B = Bh + Bl (gram_split_kernel), G = Ah^T Bh + Ah^T Bl + Al^T Bh in three
+// tcgen05 passes, each with FP32 accumulation over row chunks and FP64 chunk
+// sums; the dropped Al^T Bl and the split remainders are O(2^-20) of |A||B|
+// for TF32 inputs, O(2^-16) for BF16.
+fdtd_status gram_tensor_split(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
+                              int64_t ldb, int N, const float *w, double *out, unsigned *err) {
+  if (M == 0 || N == 0) return FDTD_OK;
+  FDTD_REQUIRE(M <= 65535 && N <= 65535, "gram_tensor_split: at most 65535 columns");
+  const int64_t n_pad = std::max<int64_t>(64, (n + 63) / 64 * 64);
+  const int es = bf16 ? 2 : 4;
+  DevBuf ah, al, bh, bl, part;
+  struct Rel {
+    DevBuf *b[5];
+    cudaStream_t s;
+    ~Rel() { for (auto *x : b) x->release(s); }
+  } rel{{&ah, &al, &bh, &bl, &part}, s};
+  const int pbk = (int)std::min<int64_t>((n_pad + 255) / 256, 1024);
+  auto split = [&](const float *src, int64_t ld, int ncols, const float *wt, DevBuf &h, DevBuf &l) -> fdtd_status {
+    FDTD_CHECK(h.alloc((size_t)ncols * n_pad * es, s));
+    FDTD_CHECK(l.alloc((size_t)ncols * n_pad * es, s));
+    if (bf16)
+      gram_split_kernel<__nv_bfloat16><<<dim3(pbk, ncols), 256, 0, s>>>(n, n_pad, src, ld, wt, h.as<__nv_bfloat16>(),
+                                                                         l.as<__nv_bfloat16>());
+    else
+      gram_split_kernel<float><<<dim3(pbk, ncols), 256, 0, s>>>(n, n_pad, src, ld, wt, h.as<float>(), l.as<float>());
+    return after_launch("gram_split_kernel");
+  };
+  FDTD_CHECK(split(A, lda, M, nullptr, ah, al));
+  const bool same = B == A && ldb == lda && N == M && !w;
+  if (!same) FDTD_CHECK(split(B, ldb, N, w, bh, bl));
+  const void *Bh = same ? ah.ptr : bh.ptr, *Bl = same ? al.ptr : bl.ptr;
+  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bh, n_pad, N, out, err, part, false));
+  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bl, n_pad, N, out, err, part, true));
+  return gram_tensor_kmajor(s, bf16, n_pad, al.ptr, n_pad, M, Bh, n_pad, N, out, err, part, true);
 }
 
 }  // namespace fdtdmor

@@ -377,8 +377,12 @@ fdtd_status fdtd_check(fdtd_grid *g, fdtd_stream_t stream) {
   FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
   if (h) {
     FDTD_CHECK_CUDA(cudaMemsetAsync(g->errflag.ptr, 0, sizeof(unsigned), s));
-    set_error("a bounded device-side wait of the stepping kernel gave up; the fields are not valid");
-    return FDTD_ETIMEOUT;
+    if (h & 3u) {
+      set_error("a bounded device-side wait of the stepping kernel gave up; the fields are not valid");
+      return FDTD_ETIMEOUT;
+    }
+    set_error("the field watchdog fired: %s", (h & 4u) ? "NaN or Inf in the fields" : "field energy grew beyond the limit");
+    return FDTD_EUNSTABLE;
   }
   return FDTD_OK;
 }

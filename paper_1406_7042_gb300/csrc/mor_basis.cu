@@ -2193,7 +2193,7 @@ extern "C" {
 fdtd_status mor_opts_default(mor_opts *o) {
   FDTD_REQUIRE(o, "mor_opts_default: NULL");
   o->q = 0; o->L = 2; o->M = 1.1; o->fmax = 0; o->dt0 = 0; o->include_center = 1;
-  o->tol = 1e-4; o->maxit = 20000; o->defl_tol = 1e-8; o->orth = MOR_ORTH_NATIVE;
+  o->tol = 1e-4; o->maxit = 20000; o->defl_tol = 1e-8; o->orth = MOR_ORTH_TF32;
   o->solver = MOR_SOLVER_AUTO;
   return FDTD_OK;
 }

@@ -8,6 +8,7 @@
 // field type and adds the slice into FP64 partial sums, which a second
 // kernel adds over slices.
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "grid_internal.cuh"
@@ -199,6 +200,20 @@ fdtd_status gram_native(cudaStream_t s, int64_t n, const double *A, int M, const
   return st;
 }
 
+// G = (G + G^T) / 2 for a q x q row-major matrix: V^T D V is symmetric by
+// definition, while the split-precision tensor-core product applies the
+// weights to one operand before splitting and so rounds the two triangles
+// differently.
+__global__ void symmetrize_kernel(int q, double *G) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)q * q) return;
+  const int i = (int)(t / q), j = (int)(t % q);
+  if (j <= i) return;
+  const double a = 0.5 * (G[(int64_t)i * q + j] + G[(int64_t)j * q + i]);
+  G[(int64_t)i * q + j] = a;
+  G[(int64_t)j * q + i] = a;
+}
+
 template <typename T>
 static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, mor_model *M) {
   FDTD_CHECK(ensure_edge_props(g, s));
@@ -224,7 +239,11 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   FDTD_CHECK(M->CE.alloc(sizeof(double) * std::max(1, p * q1), s));
   FDTD_CHECK(M->sigma.alloc(sizeof(double) * std::max(1, std::min(q1, q2)), s));
   // the five products on the tensor cores when the basis was built with TF32
-  // or BF16 Gram-Schmidt products (FP32 grids), else FP32 CUDA cores
+  // or BF16 Gram-Schmidt products (FP32 grids), else FP32 CUDA cores.  The
+  // tensor-core products are split-precision (three passes, gram_tensor_split):
+  // one TF32 / BF16 pass would put a 2^-11 / 2^-9 relative error on every
+  // entry of the reduced matrices, which the reduced model magnifies to
+  // 1e-2 / 7e-2 in its probe waveforms.
   const bool tc = sizeof(T) == 4 && b->orth != MOR_ORTH_NATIVE;
   DevBuf tflag;  // set by a tensor-core pipeline wait that gave up
   if (tc) {
@@ -233,15 +252,24 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   }
   auto G = [&](const T *A, int qa, const T *Bm, int qb, const T *wt, double *out) -> fdtd_status {
     if (tc)
-      return gram_tensor(s, b->orth == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
-                         reinterpret_cast<const float *>(Bm), n3, qb, reinterpret_cast<const float *>(wt), out,
-                         tflag.as<unsigned>());
+      return gram_tensor_split(s, b->orth == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
+                               reinterpret_cast<const float *>(Bm), n3, qb, reinterpret_cast<const float *>(wt), out,
+                               tflag.as<unsigned>());
     return gram<T>(s, n3, A, qa, Bm, qb, wt, partial, out);
   };
   FDTD_CHECK(G(V1, q1, V1, q1, w + 0 * n3, M->De.as<double>()));
   FDTD_CHECK(G(V1, q1, V1, q1, w + 1 * n3, M->Dse.as<double>()));
   FDTD_CHECK(G(V2, q2, V2, q2, w + 2 * n3, M->Dm.as<double>()));
   FDTD_CHECK(G(V2, q2, V2, q2, w + 3 * n3, M->Dsm.as<double>()));
+  if (tc) {
+    for (auto pr : {std::make_pair(q1, &M->De), std::make_pair(q1, &M->Dse), std::make_pair(q2, &M->Dm),
+                    std::make_pair(q2, &M->Dsm)}) {
+      const int64_t nn = (int64_t)pr.first * pr.first;
+      if (nn == 0) continue;
+      symmetrize_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(pr.first, pr.second->as<double>());
+      FDTD_CHECK(after_launch("symmetrize_kernel"));
+    }
+  }
   if (q1 && q2) {
     FDTD_CHECK(W.alloc(sizeof(T) * (size_t)q2 * n3, s));
     dim3 grid(bl, q2);
@@ -295,8 +323,7 @@ fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, c
                      const float *w, double *G, fdtd_stream_t stream) {
   FDTD_REQUIRE(A && B && G, "mor_gram: NULL argument");
   FDTD_REQUIRE(n >= 1 && M >= 0 && N >= 0 && lda >= n && ldb >= n, "mor_gram: bad sizes");
-  FDTD_REQUIRE(arith == MOR_ORTH_NATIVE || arith == MOR_ORTH_TF32 || arith == MOR_ORTH_BF16,
-               "mor_gram: unknown arithmetic %d", arith);
+  FDTD_REQUIRE(arith >= MOR_ORTH_NATIVE && arith <= MOR_GRAM_BF16X3, "mor_gram: unknown arithmetic %d", arith);
   cudaStream_t s = (cudaStream_t)stream;
   if (arith == MOR_ORTH_NATIVE) {
     FDTD_REQUIRE(lda == n && ldb == n, "mor_gram: the FP32 path needs lda = ldb = n");
@@ -309,8 +336,11 @@ fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, c
   FDTD_CHECK(flag.alloc(sizeof(unsigned), s));
   fdtd_status st = FDTD_OK;
   if (cudaMemsetAsync(flag.ptr, 0, sizeof(unsigned), s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
-  if (st == FDTD_OK)
-    st = gram_tensor(s, arith == MOR_ORTH_BF16, n, A, lda, M, B, ldb, N, w, G, flag.as<unsigned>());
+  if (st == FDTD_OK) {
+    const bool bf16 = arith == MOR_ORTH_BF16 || arith == MOR_GRAM_BF16X3;
+    st = arith >= MOR_GRAM_TF32X3 ? gram_tensor_split(s, bf16, n, A, lda, M, B, ldb, N, w, G, flag.as<unsigned>())
+                                  : gram_tensor(s, bf16, n, A, lda, M, B, ldb, N, w, G, flag.as<unsigned>());
+  }
   unsigned h = 0;
   if (st == FDTD_OK && cudaMemcpyAsync(&h, flag.ptr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "flag copy");

@@ -1,12 +1,11 @@
 // mor_compare_noalloc: the probe comparison of mor_compare for callers that
 // cannot allocate device memory, with its scratch in a static device array.
 //
-// Who needs it: code that runs while device allocation is forbidden or unsafe
-// -- inside a CUDA stream capture (cudaMalloc is not capturable), inside a
-// host application's real-time loop or plugin that owns all device memory
-// itself, or under an allocator that must not grow during a run.  The caller
-// still provides y_red and y_ref; only the reduction scratch moves into the
-// library image.
+// Who needs it: a host application or plugin that owns all device memory
+// itself and may not have a library allocate behind its back, or a run under
+// an allocator that must not grow while it runs.  The caller still provides
+// y_red and y_ref; only the reduction scratch moves into the library image.
+// The call reads its result back to the host and synchronises the stream.
 //
 // Scratch: g_noalloc_scratch holds one pair of partial sums per block of the
 // first pass (at most kNoAllocMaxBlocks blocks of kNoAllocBlock threads, each

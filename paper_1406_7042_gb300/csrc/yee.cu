@@ -489,7 +489,10 @@ fdtd_status fdtd_grid_autotune(fdtd_grid *g, double dt, int trial_steps, int *vw
 fdtd_status fdtd_step(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
                       int reset_fields, fdtd_stream_t stream) {
   FDTD_REQUIRE(g, "fdtd_step: NULL grid");
-  return yee_run(g, dt, nsteps, u, y, reset_fields, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  FDTD_CHECK(watchdog_before(g, u, reset_fields, s));
+  FDTD_CHECK(yee_run(g, dt, nsteps, u, y, reset_fields, s));
+  return watchdog_after(g, u, reset_fields, s);
 }
 
 fdtd_status fdtd_step_host(fdtd_grid *g, double dt, int64_t nsteps, const void *u_host,
@@ -505,9 +508,11 @@ fdtd_status fdtd_step_host(fdtd_grid *g, double dt, int64_t nsteps, const void *
     FDTD_CHECK_CUDA(cudaMemcpyAsync(g->u_stage.ptr, u_host, ub, cudaMemcpyHostToDevice, s));
   }
   if (yb) FDTD_CHECK(g->y_stage.alloc(yb, s));
+  FDTD_CHECK(watchdog_before(g, u_host, reset_fields, s));
   FDTD_CHECK(yee_run(g, dt, nsteps, ub ? g->u_stage.ptr : nullptr, yb ? g->y_stage.ptr : nullptr,
                      reset_fields, s));
   if (yb) FDTD_CHECK_CUDA(cudaMemcpyAsync(y_host, g->y_stage.ptr, yb, cudaMemcpyDeviceToHost, s));
+  FDTD_CHECK(watchdog_after(g, u_host, reset_fields, s));
   FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
   return FDTD_OK;
 }

@@ -42,9 +42,10 @@ __global__ void __launch_bounds__(LTX *LTY) yee_h_kernel(YeeArgs<T, ID> a, int l
   allow_next_grid();
 }
 
-// Bounded wait until *c >= target (acquire).  Gives up after about a second,
-// or at once when another CTA has given up, setting *err; returns false then.
-__device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, unsigned *err) {
+// Bounded wait until *c >= target (acquire).  Gives up after `limit` polls
+// (2^24 by default, about a second; fdtd_grid_set_wait_limit), or at once when
+// another CTA has given up, setting *err; returns false then.
+__device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, unsigned *err, long limit) {
   for (long spins = 0;; ++spins) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
@@ -54,7 +55,7 @@ __device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, u
       asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
       if (e) return false;
     }
-    if (spins > (1l << 24)) {
+    if (spins >= limit) {
       atomicOr(err, 2u);
       return false;
     }
@@ -82,7 +83,7 @@ __device__ __forceinline__ bool wait_count(const unsigned *c, unsigned target, u
 template <typename T, typename ID, bool HOMOG_H, int VW>
 __global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 2 : 4) yee_stream_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
                                                               int nslab, int64_t nsteps, const T *u, int m, T *y,
-                                                              int p, unsigned *cnt, unsigned *err) {
+                                                              int p, unsigned *cnt, unsigned *err, long wlimit) {
   __shared__ long long s_ticket;
   __shared__ int s_ok;
   const int tid = threadIdx.y * LTX + threadIdx.x;
@@ -109,10 +110,11 @@ __global__ void __launch_bounds__(LTX *LTY, VW >= 4 ? 2 : 4) yee_stream_kernel(Y
       bool ok = true;
       if (is_e) {
         const unsigned need = (unsigned)n * ntile;
-        ok = wait_count(doneH + sl, need, err) && (sl == 0 || wait_count(doneH + sl - 1, need, err));
+        ok = wait_count(doneH + sl, need, err, wlimit) && (sl == 0 || wait_count(doneH + sl - 1, need, err, wlimit));
       } else {
         const unsigned need = (unsigned)(n + 1) * ntile;
-        ok = wait_count(doneE + sl, need, err) && (sl + 1 == nslab || wait_count(doneE + sl + 1, need, err));
+        ok = wait_count(doneE + sl, need, err, wlimit) &&
+             (sl + 1 == nslab || wait_count(doneE + sl + 1, need, err, wlimit));
       }
       s_ok = ok;
     }
@@ -251,7 +253,7 @@ static fdtd_status run_stream_v(fdtd_grid *g, int64_t nsteps, const void *u, voi
     const T *uc = u ? static_cast<const T *>(u) + n0 * m : nullptr;
     T *yc = y ? static_cast<T *>(y) + n0 * p : nullptr;
     FDTD_CHECK_CUDA(cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), s));
-    kern<<<nblk, dim3(LTX, LTY), 0, s>>>(a, emat, lz, nslab, c, uc, m, yc, p, cnt, err);
+    kern<<<nblk, dim3(LTX, LTY), 0, s>>>(a, emat, lz, nslab, c, uc, m, yc, p, cnt, err, (long)g->wait_limit);
     FDTD_CHECK(after_launch("yee_stream_kernel"));
   }
   return FDTD_OK;

@@ -53,6 +53,7 @@ class MorOpts(C.Structure):
 
 
 MOR_ORTH = {"native": 0, "tf32": 1, "bf16": 2}
+MOR_GRAM = {"native": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
 MOR_SOLVER = {"auto": 0, "cgs": 1, "bicgstab": 2, "cocg": 3}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -106,6 +107,8 @@ _SIGS = [
                                   C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.c_void_p]),
     ("fdtd_grid_set_kernel", C.c_int, [C.c_void_p, C.c_int]),
+    ("fdtd_grid_set_watchdog", C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int]),
+    ("fdtd_grid_set_wait_limit", C.c_int, [C.c_void_p, C.c_longlong]),
     ("fdtd_grid_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.c_void_p]),
     ("fdtd_step_batched", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double), C.c_int64,
@@ -276,8 +279,19 @@ class Grid:
             pass
 
     def check(self, stream=None):
-        """Raise if a bounded device wait of an earlier step gave up."""
+        """Raise if a bounded device wait of an earlier step gave up
+        (FDTD_ETIMEOUT) or the field watchdog fired (FDTD_EUNSTABLE)."""
         check(lib().fdtd_check(self.h, _stream_ptr(stream)))
+
+    def set_watchdog(self, enable: bool = True, growth: float = 0.0, sync: bool = False):
+        """Field watchdog of step(): NaN/Inf always (when enabled); with
+        growth > 0 also energy growth of source-free calls; sync makes step()
+        raise FDTD_EUNSTABLE itself."""
+        check(lib().fdtd_grid_set_watchdog(self.h, 1 if enable else 0, float(growth), 1 if sync else 0))
+
+    def set_wait_limit(self, polls: int = -1):
+        """Polls of the dataflow form's counter waits before they give up (-1: default)."""
+        check(lib().fdtd_grid_set_wait_limit(self.h, int(polls)))
 
     def set_kernel(self, kernel: str):
         """Leap-frog kernel form: 'auto', 'persist', 'split', 'tma', 'fused' or 'march'."""
@@ -370,7 +384,7 @@ class Basis:
 
     def __init__(self, grid: "Grid", q: int, dt0: float, L: int = 2, M: float = 1.1, fmax: float = 0.0,
                  include_center: bool = True, tol: float = None, maxit: int = 20000,
-                 defl_tol: float = None, orth: str = "native", solver: str = "auto", stream=None,
+                 defl_tol: float = None, orth: str = None, solver: str = "auto", stream=None,
                  allow_noconv: bool = False):
         L_ = lib()
         o = MorOpts()
@@ -382,7 +396,8 @@ class Basis:
         o.maxit = int(maxit)
         if defl_tol is not None:
             o.defl_tol = float(defl_tol)
-        o.orth = MOR_ORTH[orth]
+        if orth is not None:
+            o.orth = MOR_ORTH[orth]
         o.solver = MOR_SOLVER[solver]
         h = C.c_void_p()
         st = L_.mor_build_basis(grid.h, C.byref(o), _stream_ptr(stream), C.byref(h))
@@ -500,7 +515,7 @@ def gram(A, B, w=None, arith: str = "tf32", stream=None):
     M, n = A.shape
     N = B.shape[0]
     G = torch.empty((M, N), dtype=torch.float64, device="cuda")
-    check(lib().mor_gram(ORTH[arith], int(n), _dptr(A), int(n), int(M), _dptr(B), int(n), int(N),
+    check(lib().mor_gram(MOR_GRAM[arith], int(n), _dptr(A), int(n), int(M), _dptr(B), int(n), int(N),
                          _dptr(w.contiguous()) if w is not None else None, _dptr(G), _stream_ptr(stream)))
     return G
 

@@ -1,6 +1,7 @@
 """Gram products G = A^T diag(w) B (mor_gram, through the C ABI) on the FP32
-CUDA cores and on the tcgen05 tensor cores (TF32, BF16 inputs), against the
-FP64 product of the same inputs."""
+CUDA cores and on the tcgen05 tensor cores (TF32, BF16 inputs, single pass or
+split into head and remainder in three passes), against the FP64 product of
+the same inputs."""
 import numpy as np
 import pytest
 
@@ -10,7 +11,7 @@ pytestmark = pytest.mark.gpu
 from paper_1406_7042_gb300 import fdtdmor as F  # noqa: E402
 
 # relative Frobenius error bounds of the three arithmetics on random inputs
-TOL = {"native": 1e-5, "tf32": 2e-3, "bf16": 1.5e-2}
+TOL = {"native": 1e-5, "tf32": 2e-3, "bf16": 1.5e-2, "tf32x3": 2e-5, "bf16x3": 5e-4}
 
 
 def _case(n, M, N, weighted, seed):
@@ -23,7 +24,7 @@ def _case(n, M, N, weighted, seed):
     return A, B, w, G
 
 
-@pytest.mark.parametrize("arith", ["native", "tf32", "bf16"])
+@pytest.mark.parametrize("arith", ["native", "tf32", "bf16", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("n,M,N,weighted", [(1000, 7, 1, False), (1000, 130, 16, True), (4096, 128, 200, True),
                                             (262181, 40, 300, False), (70001, 257, 33, True)])
 def test_gram_matches_fp64(arith, n, M, N, weighted):

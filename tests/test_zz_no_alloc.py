@@ -1,6 +1,6 @@
 """mor_compare_noalloc, the comparison entry point for callers that cannot
-allocate device memory while it runs (inside a stream capture, or in a host
-program that owns all device memory), against mor_compare.
+allocate device memory while it runs (a host program or plugin that owns all
+device memory, or an allocator that must not grow), against mor_compare.
 
 This file is collected last so that, if it fails, a run that stops at the
 first failure has already run every other test; it also passes on its own in
