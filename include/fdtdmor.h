@@ -187,6 +187,13 @@ FDTD_API fdtd_status fdtd_step_host(fdtd_grid *grid, double dt, int64_t nsteps, 
 FDTD_API fdtd_status fdtd_step_batched(fdtd_grid *const *grids, int ngrids, const double *dt, int64_t nsteps,
                               const void *const *u, void *const *y, int reset_fields, fdtd_stream_t stream);
 
+/* (e) -- z planes [k0, k0 + nk) of the six field arrays to / from a buffer
+ * laid out [6][nk][ny][nx] in the grid's type (host or device pointer), for
+ * the halo exchange of a z-slab decomposition of the grid across GPUs.
+ * Asynchronous on the stream; FDTD_EINVAL for planes outside the grid. */
+FDTD_API fdtd_status fdtd_planes_get(const fdtd_grid *grid, int k0, int nk, void *dst, fdtd_stream_t stream);
+FDTD_API fdtd_status fdtd_planes_set(fdtd_grid *grid, int k0, int nk, const void *src, fdtd_stream_t stream);
+
 /* Field watchdog of fdtd_step / fdtd_step_host (on by default, NaN/Inf
  * only): after each call the squares of the six field arrays are summed in
  * FP64; a sum that is not finite -- a leap-frog run beyond its stability

@@ -394,6 +394,31 @@ fdtd_status fdtd_fields_get(const fdtd_grid *g, void *fields6, fdtd_stream_t str
   return FDTD_OK;
 }
 
+fdtd_status fdtd_planes_get(const fdtd_grid *g, int k0, int nk, void *dst, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g && dst, "fdtd_planes_get: NULL argument");
+  FDTD_REQUIRE(k0 >= 0 && nk >= 0 && k0 + nk <= g->nz, "fdtd_planes_get: planes [%d, %d) outside 0..%d", k0, k0 + nk,
+               g->nz);
+  const size_t plane = (size_t)g->nx * g->ny * g->elem, chunk = plane * nk;
+  const char *src = static_cast<const char *>(g->fields[g->cur].ptr);
+  for (int c = 0; c < 6; ++c)
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + c * chunk, src + (size_t)c * g->nc * g->elem + k0 * plane,
+                                    chunk, cudaMemcpyDefault, (cudaStream_t)stream));
+  return FDTD_OK;
+}
+
+fdtd_status fdtd_planes_set(fdtd_grid *g, int k0, int nk, const void *src, fdtd_stream_t stream) {
+  FDTD_REQUIRE(g && src, "fdtd_planes_set: NULL argument");
+  FDTD_REQUIRE(k0 >= 0 && nk >= 0 && k0 + nk <= g->nz, "fdtd_planes_set: planes [%d, %d) outside 0..%d", k0, k0 + nk,
+               g->nz);
+  const size_t plane = (size_t)g->nx * g->ny * g->elem, chunk = plane * nk;
+  char *dst = static_cast<char *>(g->fields[g->cur].ptr);
+  for (int c = 0; c < 6; ++c)
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(dst + (size_t)c * g->nc * g->elem + k0 * plane,
+                                    static_cast<const char *>(src) + c * chunk, chunk, cudaMemcpyDefault,
+                                    (cudaStream_t)stream));
+  return FDTD_OK;
+}
+
 fdtd_status fdtd_fields_set(fdtd_grid *g, const void *fields6, fdtd_stream_t stream) {
   FDTD_REQUIRE(g && fields6, "fdtd_fields_set: NULL argument");
   FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fields[g->cur].ptr, fields6, (size_t)6 * g->nc * g->elem,

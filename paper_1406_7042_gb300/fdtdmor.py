@@ -96,6 +96,8 @@ _SIGS = [
                                  C.c_void_p]),
     ("fdtd_fields_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_fields_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("fdtd_planes_get", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    ("fdtd_planes_set", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     ("fdtd_launch_count", C.c_int64, [C.c_int]),
     ("fdtd_edge_props_get", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("fdtd_check", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -372,6 +374,19 @@ class Grid:
     def set_fields(self, f, stream=None):
         f = f.contiguous()
         check(lib().fdtd_fields_set(self.h, _dptr(f), _stream_ptr(stream)))
+
+    def planes(self, k0: int, nk: int, stream=None):
+        """(6, nk, ny, nx) device copy of z planes [k0, k0 + nk) (fdtd_planes_get)."""
+        import torch
+        s = self.spec
+        out = torch.empty((6, nk, s.ny, s.nx), dtype=self.dtype, device="cuda")
+        check(lib().fdtd_planes_get(self.h, int(k0), int(nk), _dptr(out), _stream_ptr(stream)))
+        return out
+
+    def set_planes(self, k0: int, f, stream=None):
+        """Overwrite z planes [k0, k0 + f.shape[1]) with f (6, nk, ny, nx) (fdtd_planes_set)."""
+        f = f.contiguous()
+        check(lib().fdtd_planes_set(self.h, int(k0), int(f.shape[1]), _dptr(f), _stream_ptr(stream)))
 
 
 KERNELS = {"auto": 0, "persist": 1, "split": 2, "tma": 3, "fused": 4, "march": 5}

@@ -1,0 +1,146 @@
+"""z-slab decomposition of the leap-frog and row-partitioned Gram / projection
+sums (paper_1406_7042_gb300.shard) on CPU ranks of a gloo process group.
+
+Each rank steps its slab (owned planes plus ghost planes) with the FP64
+oracle; the owned planes and the probe outputs must equal the one-grid oracle
+run bit for bit.  The partitioned sums must equal the full products."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+from oracle import mor, yee  # noqa: E402
+from paper_1406_7042_gb300 import shard  # noqa: E402
+from tests.helpers import drive, ragged_grid  # noqa: E402
+
+STEPS = 60
+
+
+def _grid():
+    g = ragged_grid(17, 13, 12, seed=41)
+    return g, 0.95 * yee.cfl_dt(g)
+
+
+class OracleSlab:
+    """Local stepper of a slab with the FP64 oracle (test side)."""
+
+    def __init__(self, spec, dt):
+        self.sys = yee.assemble(spec)
+        self.st = yee.Stepper(self.sys, dt)
+        self.e = np.zeros(self.sys.Ne)
+        self.h = np.zeros(self.sys.Nh)
+
+    def step(self, u_rows):
+        self.e, self.h = self.st.step(self.e, self.h, np.asarray(u_rows[0], np.float64))
+        y = self.sys.CE @ self.e
+        return torch.tensor(y[None, :], dtype=torch.float64)
+
+    def _arrays(self):
+        a = self.sys.to_arrays(np.concatenate([self.e, self.h]))
+        return np.stack([a[k] for k in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")])
+
+    def planes(self, k0, nk):
+        return torch.tensor(self._arrays()[:, k0:k0 + nk].copy())
+
+    def set_planes(self, k0, f):
+        a = self._arrays()
+        a[:, k0:k0 + f.shape[1]] = f.numpy()
+        x = self.sys.from_arrays({k: a[c] for c, k in enumerate(("Ex", "Ey", "Ez", "Hx", "Hy", "Hz"))})
+        self.e, self.h = x[:self.sys.Ne].copy(), x[self.sys.Ne:].copy()
+
+
+def _full_run(g, dt, u):
+    s = yee.assemble(g)
+    st = yee.Stepper(s, dt)
+    y, x, _ = st.run(u)
+    a = s.to_arrays(x)
+    return y, np.stack([a[k] for k in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")])
+
+
+def _slab_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g, dt = _grid()
+        u = drive(g, dt, STEPS)
+        st = shard.SlabStepper(g, lambda spec: OracleSlab(spec, dt))
+        y = st.run(torch.tensor(u)).numpy()
+        f = st.owned_fields().numpy()
+        yref, fref = _full_run(g, dt, u)
+        k0, k1 = st.slab.k0, st.slab.k1
+        ok_f = np.array_equal(f, fref[:, k0:k1])
+        # probe entries are summed over the ranks: equal up to that one reordering
+        ok_y = np.allclose(y, yref, rtol=1e-13, atol=1e-13 * np.abs(yref).max())
+        np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array([ok_f, ok_y, k0, k1]))
+    finally:
+        dist.destroy_process_group()
+
+
+def _gram_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g, dt = _grid()
+        s = yee.assemble(g)
+        rng = np.random.default_rng(5)
+        V1 = np.linalg.qr(rng.standard_normal((s.Ne, 9)))[0]
+        V2 = np.linalg.qr(rng.standard_normal((s.Nh, 7)))[0]
+        full = mor.project(s, V1, V2)
+        r0, r1 = shard.row_range(s.Ne, world, rank)
+        h0, h1 = shard.row_range(s.Nh, world, rank)
+        # this rank's rows of V1 (E edges) and V2 (H edges)
+        De = torch.tensor(V1[r0:r1].T @ (s.De[r0:r1, None] * V1[r0:r1]))
+        Dm = torch.tensor(V2[h0:h1].T @ (s.Dm[h0:h1, None] * V2[h0:h1]))
+        K = torch.tensor(V1[r0:r1].T @ (s.K[r0:r1] @ V2))
+        ok = all(np.allclose(shard.allreduce_sum(t).numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+                 for t, ref in ((De, full.De), (Dm, full.Dm), (K, full.K)))
+        np.save(os.path.join(out_dir, f"g{rank}.npy"), np.array([ok]))
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as sck:
+        sck.bind(("127.0.0.1", 0))
+        return sck.getsockname()[1]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_decomposition_matches_one_grid_bit_for_bit(world, tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_slab_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    cover = []
+    for r in range(world):
+        ok_f, ok_y, k0, k1 = np.load(tmp_path / f"r{r}.npy")
+        assert ok_f and ok_y, (r, ok_f, ok_y)
+        cover.append((int(k0), int(k1)))
+    g, _ = _grid()
+    assert cover[0][0] == 0 and cover[-1][1] == g.nz
+    assert all(a[1] == b[0] for a, b in zip(cover, cover[1:]))
+
+
+def test_row_partitioned_projection_sums(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_gram_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    assert all(np.load(tmp_path / f"g{r}.npy")[0] for r in range(2))
+
+
+def test_slab_ranges_and_local_grids():
+    g, _ = _grid()
+    for world in (1, 2, 3, 5, 12):
+        prev = 0
+        for r in range(world):
+            k0, k1 = shard.slab_range(g.nz, world, r)
+            assert k0 == prev and k1 > k0
+            prev = k1
+            sl = shard.local_slab(g, world, r)
+            assert sl.spec.nz == (k1 - k0) + sl.lo + sl.hi
+            assert np.array_equal(sl.spec.mat_id, g.mat_id[k0 - sl.lo:k1 + sl.hi])
+            assert len(sl.spec.ports) == len(g.ports) and len(sl.spec.probes) == len(g.probes)
+        assert prev == g.nz
+    with pytest.raises(ValueError):
+        shard.slab_range(3, 4, 0)
