@@ -125,10 +125,12 @@ FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
  * units in order from a counter and wait (bounded) only for the slabs a unit
  * depends on, so the E and H halves of a slab meet in L2.  SPLIT: an E launch
  * and an H launch per step, each thread updating 4 (FP32) or 2 (FP64)
- * consecutive x cells with vector loads when nx allows.  TMA: one fused
- * launch per step staging planes through shared memory with the tensor
- * memory accelerator (needs nx a multiple of 16 for uint8 ids, 8 for uint16).
- * FUSED: one fused launch per step with plain loads into shared memory.
+ * consecutive x cells with vector loads when nx allows.  TMA and FUSED are
+ * earlier fused designs kept as reference forms for the parity tests (AUTO
+ * never picks them; MARCH supersedes both, about 4x faster than TMA on a
+ * 384x384x64 grid): TMA stages planes through shared memory with the tensor
+ * memory accelerator, one cell per thread (nx a multiple of 16 for uint8
+ * ids, 8 for uint16); FUSED does the same with plain loads.
  * MARCH: one fused pass over memory per step: a CTA marches z over a tile of
  * 7 rows, each thread updating VW consecutive x cells (4 in FP32 on wide
  * grids) with H one plane behind E; the rows exchange E through shared memory
@@ -425,6 +427,17 @@ FDTD_API fdtd_status mor_run(mor_model *model, int64_t nsteps, const void *u, vo
 FDTD_API fdtd_status mor_model_get(const mor_model *model, int which, double *host_out, int *rows,
                                    int *cols, fdtd_stream_t stream);
 FDTD_API fdtd_status mor_model_destroy(mor_model *model);
+
+/* Save a projected model -- D~eps, D~se, D~mu, D~sm, K~ (unperturbed), B~, C~
+ * in FP64 and the grid's precision -- to a file, and load it back as a new
+ * handle that needs only mor_perturb before mor_run: one reduction serves
+ * every time step and excitation, as in the paper's tables, where one MOR
+ * time is paired with runs at several s (Tables III, V, VI).  The file holds
+ * a magic tag, a version, the sizes and the matrices in the little-endian
+ * byte order of the hosts this library builds for.  save synchronises the
+ * stream; load returns FDTD_EINVAL for a file it did not write. */
+FDTD_API fdtd_status mor_model_save(const mor_model *model, const char *path, fdtd_stream_t stream);
+FDTD_API fdtd_status mor_model_load(const char *path, fdtd_stream_t stream, mor_model **out);
 
 /* A12 (reduced model) -- gradient of a probe loss of the reduced leap-frog
  * (Eq. (R_and_Freduced) as prepared by mor_perturb) with respect to eps_r,

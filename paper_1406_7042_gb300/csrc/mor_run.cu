@@ -14,6 +14,8 @@
 // memory, with one cluster barrier per phase.  Models too large for 16 CTAs
 // stream the matrices from L2 in the one-CTA kernel.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
 #include <cooperative_groups.h>
 #include <cstdlib>
 #include <string>
@@ -314,6 +316,85 @@ fdtd_status mor_model_get(const mor_model *M, int which, double *host_out, int *
     FDTD_CHECK_CUDA(cudaMemcpyAsync(host_out, src->ptr, sizeof(double) * r * c, cudaMemcpyDeviceToHost, s));
     FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
   }
+  return FDTD_OK;
+}
+
+// File of a projected model: "FDTDMOR1", int32 version (1), q1, q2, m, p,
+// prec, then the FP64 matrices D~eps, D~se (q1 x q1), D~mu, D~sm (q2 x q2),
+// K~ (q1 x q2), B~_E (q1 x m), B~_H (q2 x m), C~_E (p x q1), row-major, in
+// the little-endian byte order of the hosts this library builds for.
+static const char kModelMagic[8] = {'F', 'D', 'T', 'D', 'M', 'O', 'R', '1'};
+
+fdtd_status mor_model_save(const mor_model *M, const char *path, fdtd_stream_t stream) {
+  FDTD_REQUIRE(M && path, "mor_model_save: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t hdr[6] = {1, M->q1, M->q2, M->m, M->p, (int32_t)M->prec};
+  const DevBuf *bufs[8] = {&M->De, &M->Dse, &M->Dm, &M->Dsm, &M->K, &M->BE, &M->BH, &M->CE};
+  const size_t cnt[8] = {(size_t)M->q1 * M->q1, (size_t)M->q1 * M->q1, (size_t)M->q2 * M->q2, (size_t)M->q2 * M->q2,
+                         (size_t)M->q1 * M->q2, (size_t)M->q1 * M->m, (size_t)M->q2 * M->m, (size_t)M->p * M->q1};
+  std::vector<double> host;
+  for (int i = 0; i < 8; ++i) {
+    const size_t off = host.size();
+    host.resize(off + cnt[i]);
+    if (cnt[i]) FDTD_CHECK_CUDA(cudaMemcpyAsync(host.data() + off, bufs[i]->ptr, cnt[i] * sizeof(double),
+                                                cudaMemcpyDeviceToHost, s));
+  }
+  FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+  FILE *f = fopen(path, "wb");
+  FDTD_REQUIRE(f, "mor_model_save: cannot open %s for writing", path);
+  const bool ok = fwrite(kModelMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+                  (host.empty() || fwrite(host.data(), sizeof(double), host.size(), f) == host.size());
+  const bool closed = fclose(f) == 0;
+  FDTD_REQUIRE(ok && closed, "mor_model_save: write to %s failed", path);
+  return FDTD_OK;
+}
+
+fdtd_status mor_model_load(const char *path, fdtd_stream_t stream, mor_model **out) {
+  FDTD_REQUIRE(path && out, "mor_model_load: NULL argument");
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  FDTD_REQUIRE(f, "mor_model_load: cannot open %s", path);
+  char magic[8];
+  int32_t hdr[6];
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kModelMagic, 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+            hdr[0] == 1 && hdr[1] >= 0 && hdr[2] >= 0 && hdr[3] >= 0 && hdr[4] >= 0 &&
+            (hdr[5] == FDTD_F32 || hdr[5] == FDTD_F64) && hdr[1] <= 65535 && hdr[2] <= 65535;
+  const int q1 = ok ? hdr[1] : 0, q2 = ok ? hdr[2] : 0, m = ok ? hdr[3] : 0, p = ok ? hdr[4] : 0;
+  const size_t cnt[8] = {(size_t)q1 * q1, (size_t)q1 * q1, (size_t)q2 * q2, (size_t)q2 * q2,
+                         (size_t)q1 * q2, (size_t)q1 * m, (size_t)q2 * m, (size_t)p * q1};
+  size_t total = 0;
+  for (size_t c : cnt) total += c;
+  std::vector<double> host(ok ? total : 0);
+  if (ok && total) ok = fread(host.data(), sizeof(double), total, f) == total;
+  fclose(f);
+  FDTD_REQUIRE(ok, "mor_model_load: %s is not a reduced-model file of this library", path);
+  cudaStream_t s = (cudaStream_t)stream;
+  mor_model *M = new mor_model();
+  M->q1 = q1; M->q2 = q2; M->m = m; M->p = p;
+  M->prec = (fdtd_prec)hdr[5];
+  M->elem = M->prec == FDTD_F64 ? 8 : 4;
+  M->stream = s;
+  DevBuf *bufs[8] = {&M->De, &M->Dse, &M->Dm, &M->Dsm, &M->K, &M->BE, &M->BH, &M->CE};
+  fdtd_status st = FDTD_OK;
+  size_t off = 0;
+  for (int i = 0; i < 8 && st == FDTD_OK; ++i) {
+    st = bufs[i]->alloc(sizeof(double) * std::max<size_t>(1, cnt[i]), s);
+    if (st == FDTD_OK && cnt[i] &&
+        cudaMemcpyAsync(bufs[i]->ptr, host.data() + off, cnt[i] * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "mor_model_load copy");
+    off += cnt[i];
+  }
+  if (st == FDTD_OK) st = M->Kp.alloc(sizeof(double) * std::max<size_t>(1, cnt[4]), s);
+  if (st == FDTD_OK && cnt[4] &&
+      cudaMemcpyAsync(M->Kp.ptr, M->K.ptr, cnt[4] * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "mor_model_load copy");
+  if (st == FDTD_OK) st = M->sigma.alloc(sizeof(double) * std::max(1, std::min(q1, q2)), s);
+  if (st == FDTD_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
+  if (st != FDTD_OK) {
+    mor_model_destroy(M);
+    return st;
+  }
+  *out = M;
   return FDTD_OK;
 }
 

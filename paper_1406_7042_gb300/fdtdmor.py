@@ -138,6 +138,8 @@ _SIGS = [
     ("mor_model_get", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.c_void_p]),
     ("mor_model_destroy", C.c_int, [C.c_void_p]),
+    ("mor_model_save", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
+    ("mor_model_load", C.c_int, [C.c_char_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_gradient", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     ("mor_compare", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
@@ -462,6 +464,22 @@ class Model:
         self.h = h
         self.grid = grid
         _track(self)
+
+    def save(self, path: str, stream=None):
+        """Write the projected (unperturbed) model to a file (mor_model_save)."""
+        check(lib().mor_model_save(self.h, os.fsencode(path), _stream_ptr(stream)))
+
+    @classmethod
+    def load(cls, path: str, grid: "Grid", stream=None) -> "Model":
+        """A model read back from mor_model_save's file, for the grid it was
+        reduced from (whose sources, probes and precision it carries)."""
+        h = C.c_void_p()
+        check(lib().mor_model_load(os.fsencode(path), _stream_ptr(stream), C.byref(h)))
+        self = cls.__new__(cls)
+        self.h = h
+        self.grid = grid
+        _track(self)
+        return self
 
     def perturb(self, dt: float, gamma: float = 0.9999, stream=None) -> int:
         n = C.c_int()

@@ -398,6 +398,33 @@ def test_tensor_core_projection_matches_oracle(orth, mat_tol):
         assert mor.rel_l2(yg, yo) <= TOL_RED_F32, (kk, mor.rel_l2(yg, yo))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_model_save_load_reuses_one_reduction(prec, tmp_path):
+    """mor_model_save / mor_model_load: the reloaded model carries the same
+    projected matrices bit for bit, and perturbed and stepped at several s it
+    gives the same probe waveforms as the model it was saved from."""
+    g = _lossy_ragged()
+    grid = F.Grid(g, prec)
+    dt0 = 0.99 * grid.cfl_dt()
+    gb = F.Basis(grid, 12, dt0, 1, 1.1, 60e9, tol=1e-10 if prec == "f64" else 1e-5)
+    model = F.Model(grid, gb)
+    path = str(tmp_path / "model.bin")
+    model.save(path)
+    back = F.Model.load(path, grid)
+    for name in ("De", "Dse", "Dm", "Dsm", "K", "BE", "CE"):
+        assert np.array_equal(back.get(name), model.get(name)), name
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    for k in (1, 3, 6):
+        dt = k * dt0
+        u = torch.tensor(drive(g, dt, 200), dtype=dtype, device="cuda")
+        assert model.perturb(dt, GAMMA) == back.perturb(dt, GAMMA)
+        assert torch.equal(model.run(u), back.run(u)), k
+    with open(path, "r+b") as f:
+        f.write(b"NOTAMODL")
+    with pytest.raises(F.FdtdError):
+        F.Model.load(path, grid)
+
+
 def test_lossy_multiport_moments_and_stages_f64():
     """Two ports (block Arnoldi across ports), loss, PEC blocks, graded cells:
     the GPU model matches the full system's moments at every point, and

@@ -228,3 +228,24 @@ def test_cavity10_reduced_error_small(cav10):
     yref, _, _ = yee.Stepper(s, dt0).run(u)
     y = mor.reduced_run(red, dt0, u)
     assert mor.rel_l2(y, yref) < 1e-5
+
+
+def test_moments_pinned_to_transfer_function_derivatives():
+    """moments_full about z_l against the Taylor coefficients of the transfer
+    function itself: with G(z) = H(z)/z = C A(z)^{-1} B and dA/dz = R + F,
+    M_j = (-1)^j G^(j)(z_l)/j!, taken from transfer_full on a circle around
+    z_l by the Cauchy integral (trapezoid rule, spectrally accurate) -- a
+    wrong chain operator or sign fails it."""
+    from tests.helpers import ragged_grid
+    g = ragged_grid(12, 10, 9, seed=13)
+    s = yee.assemble(g)
+    dt = 0.9 * yee.cfl_dt(g)
+    for z in (1.1 + 0j, 1.1 * np.exp(0.3j)):
+        rho, npts, count = 0.03, 24, 4
+        th = 2 * np.pi * np.arange(npts) / npts
+        Gs = [mor.transfer_full(s, dt, z + rho * np.exp(1j * t)) / (z + rho * np.exp(1j * t)) for t in th]
+        mom = mor.moments_full(s, dt, z, count)
+        for j in range(count):
+            taylor = sum(G * np.exp(-1j * j * t) for G, t in zip(Gs, th)) / npts / rho ** j
+            ref = (-1) ** j * taylor
+            assert np.max(np.abs(mom[j] - ref)) <= 1e-6 * np.max(np.abs(ref)), (z, j)

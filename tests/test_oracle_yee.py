@@ -282,3 +282,38 @@ def test_matched_absorber_reduces_reflection():
     ratio_m = absorbed.sig_m[new] / (W.MU0 * absorbed.mu_r[new])
     ratio_e = absorbed.sig_e[new] / (W.EPS0 * absorbed.eps_r[new])
     assert np.allclose(ratio_m, ratio_e, rtol=1e-12)
+
+
+def _exact_dt_uniform(N, d, c):
+    """Largest stable dt of the leap-frog on a uniform box from the discrete
+    dispersion relation sin^2(w dt/2)/(c dt)^2 = sum_i sin^2(m_i pi/(2 N_i))/d_i^2
+    at its highest mode m_i = N_i - 1 (the right side times (c dt)^2 <= 1)."""
+    s = sum(np.sin((n - 1) * np.pi / (2 * n)) ** 2 / di ** 2 for n, di in zip(N, d))
+    return 1.0 / (c * np.sqrt(s))
+
+
+def test_cfl_dt_pinned_to_dispersion_limit():
+    """Eq. (CFL) against the exact limit of the discrete dispersion relation:
+    on uniform anisotropic boxes the exact limit from the highest mode equals
+    the oracle's power-iteration limit (small box, 1e-9) and approaches
+    Eq. (CFL) from above as the box grows (within (pi/2N)^2 / 2 at N = 60);
+    a uniform eps_r = 4 fill scales both by exactly 2."""
+    from paper_1406_7042_gb300 import workloads as W
+    c0 = yee.C0
+
+    def box(N, d, eps_r=1.0):
+        eps, mu, se, sm, pec = W.vacuum_table([(eps_r, 0.0)])
+        nx, ny, nz = N
+        return W.GridSpec(nx, ny, nz, np.full(nx, d[0]), np.full(ny, d[1]), np.full(nz, d[2]), eps, mu, se, sm, pec,
+                          np.full((nz, ny, nx), 2 if eps_r != 1.0 else 0, np.uint16))
+
+    N, d = (6, 5, 4), (1e-3, 0.7e-3, 1.3e-3)
+    ex = _exact_dt_uniform(N, d, c0)
+    assert abs(yee.exact_dt_limit(yee.assemble(box(N, d))) / ex - 1) < 1e-9
+    assert yee.cfl_dt(box(N, d)) <= ex
+    N = (60, 70, 80)
+    ex = _exact_dt_uniform(N, d, c0)
+    cfl = yee.cfl_dt(box(N, d))
+    assert cfl <= ex and ex / cfl - 1 < 0.5 * (np.pi / (2 * 60)) ** 2
+    assert abs(yee.cfl_dt(box(N, d, 4.0)) / cfl - 2.0) < 1e-14
+    assert abs(_exact_dt_uniform(N, d, c0 / 2) / ex - 2.0) < 1e-14
