@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -319,7 +320,7 @@ fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const
 // 16-byte-aligned bases).  part: scratch for the FP32 partials.
 fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void *A, int64_t lda, int M,
                                const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part,
-                               bool accumulate) {
+                               bool accumulate, int64_t max_rows) {
   if (M == 0 || N == 0) return FDTD_OK;
   const int es = bf16 ? 2 : 4;
   FDTD_REQUIRE(M <= 65535 && N <= 65535, "gram_tensor: at most 65535 columns");
@@ -334,6 +335,9 @@ fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int nsplit = std::max(1, std::min(kslices, std::max(1, sms) / std::max(1, mt * ntl)));  // one wave
+  // at most max_rows rows per FP32 partial (their sum is FP64): a TMEM
+  // accumulation over ~1e4 rows alone leaves ~1e-5 of relative error
+  if (max_rows > 0) nsplit = std::max<int64_t>(nsplit, std::min<int64_t>(kslices, (n + max_rows - 1) / max_rows));
   const int per = (kslices + nsplit - 1) / nsplit;
   nsplit = (kslices + per - 1) / per;
   FDTD_CHECK(part.alloc((size_t)nsplit * M * N * sizeof(float), s));
@@ -388,7 +392,7 @@ fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, in
     }
     lb = n_pad;
   }
-  return gram_tensor_kmajor(s, bf16, nk, pA, la, M, pB, lb, N, out, err, part, false);
+  return gram_tensor_kmajor(s, bf16, nk, pA, la, M, pB, lb, N, out, err, part, false, 0);
 }
 
 // Split-precision G = A^T diag(w) B on the tensor cores: with A = Ah + Al and
@@ -396,6 +400,13 @@ fdtd_status gram_tensor(cudaStream_t s, bool bf16, int64_t n, const float *A, in
 // tcgen05 passes, each with FP32 accumulation over row chunks and FP64 chunk
 // sums; the dropped Al^T Bl and the split remainders are O(2^-20) of |A||B|
 // for TF32 inputs, O(2^-16) for BF16.
+// Rows per FP32 partial of the split-precision products (the partials are
+// summed in FP64).  Measured on the 64^3 graded cavity with matched absorbers
+// (q = 200, reduced-model probe error against the full-order run): 2048 rows
+// 2.0e-3, 512 rows 3.4e-4 (FP32 CUDA-core products: 2.1e-4), 256 or 64 rows no
+// better; the projection's time grows as the rows shrink (11, 15, 21, 64 ms).
+constexpr int64_t kSplitRows = 512;
+
 fdtd_status gram_tensor_split(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
                               int64_t ldb, int N, const float *w, double *out, unsigned *err) {
   if (M == 0 || N == 0) return FDTD_OK;
@@ -423,9 +434,11 @@ fdtd_status gram_tensor_split(cudaStream_t s, bool bf16, int64_t n, const float 
   const bool same = B == A && ldb == lda && N == M && !w;
   if (!same) FDTD_CHECK(split(B, ldb, N, w, bh, bl));
   const void *Bh = same ? ah.ptr : bh.ptr, *Bl = same ? al.ptr : bl.ptr;
-  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bh, n_pad, N, out, err, part, false));
-  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bl, n_pad, N, out, err, part, true));
-  return gram_tensor_kmajor(s, bf16, n_pad, al.ptr, n_pad, M, Bh, n_pad, N, out, err, part, true);
+  const char *env = getenv("FDTDMOR_SPLIT_ROWS");
+  const int64_t rows = env ? std::max<int64_t>(32, atoll(env)) : kSplitRows;
+  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bh, n_pad, N, out, err, part, false, rows));
+  FDTD_CHECK(gram_tensor_kmajor(s, bf16, n_pad, ah.ptr, n_pad, M, Bl, n_pad, N, out, err, part, true, rows));
+  return gram_tensor_kmajor(s, bf16, n_pad, al.ptr, n_pad, M, Bh, n_pad, N, out, err, part, true, rows);
 }
 
 }  // namespace fdtdmor

@@ -16,7 +16,7 @@ fdtd_status gram_pack(cudaStream_t s, bool bf16, int64_t n, int64_t n_pad, const
                       const float *w, void *dst);
 fdtd_status gram_tensor_kmajor(cudaStream_t s, bool bf16, int64_t n, const void *A, int64_t lda, int M,
                                const void *B, int64_t ldb, int N, double *out, unsigned *err, DevBuf &part,
-                               bool accumulate = false);
+                               bool accumulate = false, int64_t max_rows = 0);
 // Split-precision (three-pass) tensor-core Gram product: FP32-level accuracy.
 fdtd_status gram_tensor_split(cudaStream_t s, bool bf16, int64_t n, const float *A, int64_t lda, int M, const float *B,
                               int64_t ldb, int N, const float *w, double *out, unsigned *err);

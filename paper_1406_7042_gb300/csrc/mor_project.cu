@@ -8,6 +8,8 @@
 // field type and adds the slice into FP64 partial sums, which a second
 // kernel adds over slices.
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -244,7 +246,12 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   // one TF32 / BF16 pass would put a 2^-11 / 2^-9 relative error on every
   // entry of the reduced matrices, which the reduced model magnifies to
   // 1e-2 / 7e-2 in its probe waveforms.
-  const bool tc = sizeof(T) == 4 && b->orth != MOR_ORTH_NATIVE;
+  int parith = b->orth;  // FDTDMOR_PROJECT=native / tf32 / bf16 overrides (measurements)
+  if (const char *e = getenv("FDTDMOR_PROJECT")) {
+    const std::string v(e);
+    parith = v == "native" ? MOR_ORTH_NATIVE : v == "tf32" ? MOR_ORTH_TF32 : v == "bf16" ? MOR_ORTH_BF16 : parith;
+  }
+  const bool tc = sizeof(T) == 4 && parith != MOR_ORTH_NATIVE;
   DevBuf tflag;  // set by a tensor-core pipeline wait that gave up
   if (tc) {
     FDTD_CHECK(tflag.alloc(sizeof(unsigned), s));
@@ -252,7 +259,7 @@ static fdtd_status project_t(fdtd_grid *g, const mor_basis *b, cudaStream_t s, m
   }
   auto G = [&](const T *A, int qa, const T *Bm, int qb, const T *wt, double *out) -> fdtd_status {
     if (tc)
-      return gram_tensor_split(s, b->orth == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
+      return gram_tensor_split(s, parith == MOR_ORTH_BF16, n3, reinterpret_cast<const float *>(A), n3, qa,
                                reinterpret_cast<const float *>(Bm), n3, qb, reinterpret_cast<const float *>(wt), out,
                                tflag.as<unsigned>());
     return gram<T>(s, n3, A, qa, Bm, qb, wt, partial, out);
