@@ -325,6 +325,8 @@ def run_ours(args):
             line["reduce_run"]["study"] = reduction_study(F, W, wl, grid, y, dt0, fdtd_ms / args.steps)
     if rank == 0 and args.config4:
         line["config4_full"] = config4_full(F, W)
+    if rank == 0 and args.paper_cases:
+        line["paper_cases"] = paper_cases(F, W)
     if rank == 0 and args.hbm_grid:
         line["yee_hbm"] = hbm_grid_measure(F, W, hbm)
         line["config"]["hbm_bound_yee"] = {k: line["yee_hbm"][k] for k in
@@ -629,6 +631,85 @@ def config4_full(F, W):
     return rec
 
 
+# The paper's own timing tables (MATLAB, machine not stated; seconds): FDTD
+# total and proposed-method total per s (Tables II, III and IV).
+PAPER_TIMES = {
+    "cavity2d": {"fdtd_s": 4.71, "proposed_s": {"0.99": 1.09, "4.95": 0.88}},
+    "cavity3d": {"fdtd_s": 346.52, "proposed_s": {"0.99": 103.04, "1.98": 102.91, "2.97": 102.88}},
+    "waveguide2d": {"fdtd_s": 37.18, "proposed_s": {"0.99": 3.31, "4.95": 2.31, "8.91": 2.20}},
+}
+
+
+def paper_cases(F, W):
+    """The paper's 2-D cavity, 3-D cavity (Sec. V-A, Table I) and 2-D
+    waveguide filter (Sec. V-B) on the GPU in FP32: full-order run, reduction
+    (five points, M = 1.1), reduced runs at the paper's s, with the times in the
+    paper's Setup / MOR / Run / Total form against the GPU's own FDTD, the
+    probe error against it, the first cavity resonances against the analytic
+    values, and |S21|, |S11| of the guide against a reference run of the line
+    without irises."""
+    import torch
+    out = {}
+    cases = (("cavity2d", W.cavity2d_workload(), (1.01, 1.01, None), (1, 5)),
+             ("cavity3d", W.cavity3d_workload(), (1.02, 1.02, 1.02), (1, 2, 3)),
+             ("waveguide2d", W.waveguide2d_workload(), None, (1, 5, 9)))
+    for name, wl, sides, ks in cases:
+        g = wl.grid
+        grid, t_setup = _timed(lambda: F.Grid(g, "f32"))
+        dt0 = wl.s_ref * grid.cfl_dt()
+        u = torch.tensor(W.excitation(g, wl.f0, wl.bw, dt0, wl.nsteps_ref).astype(np.float32), device="cuda")
+        grid.step(dt0, u[:50].contiguous(), reset=True)
+        y, t_fd = _timed(lambda: grid.step(dt0, u, reset=True))
+        rec = {"grid": [g.nx, g.ny, g.nz], "steps": wl.nsteps_ref, "q": wl.q, "M": wl.M, "fmax_hz": wl.fmax,
+               "setup_ms": round(t_setup, 1), "fdtd_ms": round(t_fd, 2), "paper_matlab_s": PAPER_TIMES[name]}
+        if sides is not None:
+            fa = W.cavity_resonances(*sides, count=6)
+            pk = F.resonances(y, dt0, 0.05e9, 0.7e9, nf=8000, hann=True, rel_floor=0.02, npk=40)
+            e = np.array([np.min(np.abs(pk - f)) / f for f in fa])
+            seen = e < 0.01
+            rec["analytic_ghz"] = [round(f / 1e9, 5) for f in fa]
+            rec["fdtd_resonance_err"] = [round(float(v), 6) if ok else None for v, ok in zip(e, seen)]
+        else:
+            ref = F.Grid(W.waveguide2d_workload(irises=False).grid, "f32")
+            yinc = ref.step(dt0, u, reset=True)
+            freqs = np.linspace(2.0e9, 4.0e9, 81)
+            Yi = F.dft(yinc, dt0, freqs)
+            Yf = F.dft(y, dt0, freqs)
+            S_fd = np.abs(np.stack([(Yf[0] - Yi[0]) / Yi[0], Yf[1] / Yi[0]]))
+            rec["s21_fdtd_max"] = round(float(S_fd[1].max()), 4)
+            rec["s21_fdtd_argmax_ghz"] = round(float(freqs[int(S_fd[1].argmax())] / 1e9), 3)
+            ref.close()
+        basis, t_b = _timed(lambda: F.Basis(grid, wl.q, dt0, wl.L, wl.M, wl.fmax, tol=1e-4))
+        model, t_p = _timed(lambda: F.Model(grid, basis))
+        inf = basis.info()
+        rec.update(mor_ms=round(t_b + t_p, 1), q1=inf["q1"], q2=inf["q2"], max_rel_residual=inf["max_resid"])
+        rec["by_s"] = {}
+        for k in ks:
+            dt = k * dt0
+            ns = wl.nsteps_ref // k
+            _, t_pt = _timed(lambda: model.perturb(dt))
+            uu = torch.tensor(W.excitation(g, wl.f0, wl.bw, dt, ns).astype(np.float32), device="cuda")
+            yr, t_r = _timed(lambda: model.run(uu))
+            total = t_setup + t_b + t_p + t_pt + t_r
+            r = {"run_ms": round(t_pt + t_r, 2), "total_ms": round(total, 1),
+                 "speedup_vs_gpu_fdtd": round((t_setup + t_fd) / total, 3),
+                 "probe_err_vs_fdtd": round(F.compare(yr, y, k, k - 1), 5)}
+            if sides is not None:
+                pk = F.resonances(yr, dt, 0.05e9, 0.7e9, nf=8000, hann=True, rel_floor=0.02, npk=40)
+                r["resonance_err"] = [round(float(np.min(np.abs(pk - f)) / f), 6) if ok else None
+                                      for f, ok in zip(fa, seen)]
+            else:
+                Yr = F.dft(yr, dt, freqs)
+                S_r = np.abs(np.stack([(Yr[0] - Yi[0]) / Yi[0], Yr[1] / Yi[0]]))
+                r["s21_max_abs_diff"] = round(float(np.max(np.abs(S_r[1] - S_fd[1]))), 4)
+                r["s11_max_abs_diff"] = round(float(np.max(np.abs(S_r[0] - S_fd[0]))), 4)
+            rec["by_s"][f"s={round(0.99 * k, 2)}"] = r
+        out[name] = rec
+        del model, basis
+        grid.close()
+    return out
+
+
 def hbm_grid_measure(F, W, hbm, nsteps=200):
     """Yee kernel alone on the 384x384x64 metascreen grid (453 MB state, HBM-bound)."""
     import torch
@@ -741,6 +822,7 @@ def main():
     ap.add_argument("--mor", type=int, default=1, help="include the reduction stages in the bench step")
     ap.add_argument("--study", type=int, default=1, help="reduce+run at other settings (q, M, absorbers)")
     ap.add_argument("--config4", type=int, default=1, help="the 400x200x24 microstrip at q = 400")
+    ap.add_argument("--paper-cases", type=int, default=1, help="the paper's 2-D / 3-D cavities and 2-D guide")
     ap.add_argument("--tol", type=float, default=1e-4, help="shifted-solve residual limit (Sec. IV-B: 1e-4)")
     ap.add_argument("--defl-tol", type=float, default=1e-5)
     ap.add_argument("--only-yee", default="", choices=["", "graded", "metascreen", "cavity10"])

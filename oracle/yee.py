@@ -308,7 +308,10 @@ def assemble(grid) -> YeeSystem:
 # ------------------------------------------------------------------ Eq. (CFL)
 def cfl_dt(grid) -> float:
     """Eq. (CFL) with the fastest wave speed c0 / sqrt(min eps_r mu_r) and the
-    smallest cell on each axis (conservative reading for graded grids)."""
+    smallest cell on each axis (conservative reading for graded grids).  A
+    single layer of cells between the z plates (nz = 1) is the 2-D TM problem
+    of Sec. V-A/V-B: no update differences along z, so Eq. (CFL) has only the
+    x and y terms."""
     er = np.asarray(grid.eps_r, np.float64)
     mr = np.asarray(grid.mu_r, np.float64)
     used = np.unique(grid.mat_id)
@@ -316,7 +319,8 @@ def cfl_dt(grid) -> float:
     emin = min(er[u] * mr[u] for u in nonpec) if nonpec else 1.0
     c = C0 / math.sqrt(emin)
     dxm, dym, dzm = float(np.min(grid.dx)), float(np.min(grid.dy)), float(np.min(grid.dz))
-    return 1.0 / (c * math.sqrt(1.0 / dxm ** 2 + 1.0 / dym ** 2 + 1.0 / dzm ** 2))
+    zterm = 0.0 if grid.nz == 1 else 1.0 / dzm ** 2
+    return 1.0 / (c * math.sqrt(1.0 / dxm ** 2 + 1.0 / dym ** 2 + zterm))
 
 
 def exact_dt_limit(sys: YeeSystem) -> float:

@@ -168,7 +168,10 @@ static void derive_material_props(fdtd_grid *g) {
   double dxm = *std::min_element(g->dx.begin(), g->dx.end());
   double dym = *std::min_element(g->dy.begin(), g->dy.end());
   double dzm = *std::min_element(g->dz.begin(), g->dz.end());
-  g->cfl = 1.0 / ((kC0 / std::sqrt(emin)) * std::sqrt(1 / (dxm * dxm) + 1 / (dym * dym) + 1 / (dzm * dzm)));
+  // a single layer between the z plates (nz = 1) is the 2-D TM problem: no
+  // update differences along z, so Eq. (CFL) keeps only the x and y terms
+  const double zterm = g->nz == 1 ? 0.0 : 1 / (dzm * dzm);
+  g->cfl = 1.0 / ((kC0 / std::sqrt(emin)) * std::sqrt(1 / (dxm * dxm) + 1 / (dym * dym) + zterm));
 }
 
 // Raw table (eps_r, sig_e, mu_r, sig_m, pec; 5 x nmat doubles) on the device

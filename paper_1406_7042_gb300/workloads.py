@@ -335,6 +335,101 @@ def waveguide_workload(seed: int = SEED_BASE + 3, absorbing: bool = False) -> Wo
                     fmax=45e9, s_red=[0.99], nsteps_red=[20000], precision="f32")
 
 
+# ---------------------------------------------------------------- the paper's cavities and 2-D guide
+def plates2d(nx: int, ny: int, d: float, eps_r: float = 1.0) -> GridSpec:
+    """A 2-D TM problem (Ez, Hx, Hy) as one layer of cells between two PEC
+    plates: with nz = 1 the tangential Ex, Ey and the normal Hz vanish on the
+    plates, leaving (nx-1)(ny-1) Ez, (nx-1) ny Hx and nx (ny-1) Hy unknowns."""
+    eps, mu, se, sm, pec = vacuum_table([(eps_r, 0.0)] if eps_r != 1.0 else None)
+    mat = np.full((1, ny, nx), 2 if eps_r != 1.0 else 0, np.uint16)
+    return GridSpec(nx, ny, 1, _uniform(nx, d), _uniform(ny, d), _uniform(1, d), eps, mu, se, sm, pec, mat)
+
+
+def cavity2d_workload(seed: int = SEED_BASE + 6) -> Workload:
+    """The 2-D PEC cavity of Sec. V-A (Table I): 101 x 101 cells of 1 cm, a
+    single source and probe (Ez, seeded interior nodes), a pulse of bandwidth
+    0.5 GHz centred at 0.35 GHz (its -20 dB band holds the first six TM
+    resonances but for the sixth at 0.61 GHz), 10,000 steps; q = 80 with five
+    expansion points, M = 1.1, fmax = 0.6 GHz; reduced at s = 0.99 and 4.95."""
+    rng = np.random.default_rng(seed)
+    g = plates2d(101, 101, 1e-2)
+    used = set()
+    for lst in (g.ports, g.probes):
+        i, j, _ = _distinct_cell(rng, used, (101, 101, 1), 5)
+        lst.append(Port.point(COMP_EZ, i, j, 0))
+    return Workload("cavity2d_f32", g, 0.99, 10000, 0.35e9, 0.5e9, q=80, L=2, M=1.1, fmax=0.6e9,
+                    s_red=[0.99, 4.95], nsteps_red=[10000, 2000], precision="f32")
+
+
+def cavity3d_workload(seed: int = SEED_BASE + 7) -> Workload:
+    """The 3-D PEC cavity of Sec. V-A (Table I): 51^3 cells of 2 cm, a single
+    Ez source and probe at seeded interior cells, the same pulse (the first
+    six resonances, 0.21-0.44 GHz, inside its band), 10,000 steps; q = 80,
+    five expansion points, M = 1.1, fmax = 0.5 GHz; reduced at s = 0.99,
+    1.98, 2.97."""
+    g = cavity_uniform(51, 2e-2, seed)
+    return Workload("cavity3d_f32", g, 0.99, 10000, 0.35e9, 0.5e9, q=80, L=2, M=1.1, fmax=0.5e9,
+                    s_red=[0.99, 1.98, 2.97], nsteps_red=[10000, 5000, 3333], precision="f32")
+
+
+def cavity_resonances(a: float, b: float, c: float = None, count: int = 6) -> np.ndarray:
+    """Lowest distinct resonance frequencies (Hz) of an empty PEC box of sides
+    a, b (and c; 2-D TM when None): f = c0/2 sqrt((m/a)^2 + (n/b)^2 + (p/c)^2),
+    m, n >= 1 in 2-D; in 3-D at most one index zero (TE and TM together)."""
+    c0 = 299792458.0
+    fs = set()
+    rng = range(0, 12)
+    for m in rng:
+        for n in rng:
+            if c is None:
+                if m >= 1 and n >= 1:
+                    fs.add(round(c0 / 2 * np.sqrt((m / a) ** 2 + (n / b) ** 2), 3))
+                continue
+            for p_ in rng:
+                if (m == 0) + (n == 0) + (p_ == 0) <= 1:
+                    fs.add(round(c0 / 2 * np.sqrt((m / a) ** 2 + (n / b) ** 2 + (p_ / c) ** 2), 3))
+    return np.array(sorted(fs)[:count])
+
+
+def waveguide2d(irises: bool = True, d: float = 1.25e-3) -> GridSpec:
+    """The 2-D waveguide filter of Sec. V-B as a TM problem between plates:
+    5 cm x 50 cm (41 x 401 cells of 1.25 mm) filled with eps_r = 2.5, five
+    thin PEC irises across the guide (one cell thick, an aperture of 8 cells =
+    1 cm at the centre, 40 cells = 5 cm apart, centred on the guide; the
+    layout figure is not available and "length 1.25 cm" is read as the
+    cross-section of each iris wall), 5-cell 4th-order matched absorbers at
+    both ends, an Ez current line across the guide at y = 8 (TM1 profile),
+    line probes at y = 12 (port 1) and y = 392 (port 2).  Without irises it
+    is the matched reference line of the S-parameters."""
+    nx, ny = 41, 401
+    g = plates2d(nx, ny, d, 2.5)   # material 2: the filling; 1: PEC
+    if irises:
+        x0 = (nx - 8) // 2
+        for t in range(5):
+            y0 = ny // 2 + (t - 2) * 40
+            g.mat_id[0, y0, :] = 1
+            g.mat_id[0, y0, x0:x0 + 8] = 2
+    g = add_absorber(g, "yY")
+    xs = np.arange(1, nx, dtype=np.int64)
+    prof = np.sin(np.pi * xs / nx)
+
+    def line(y, w):
+        return Port(COMP_EZ, np.zeros(xs.size, np.int64), np.full(xs.size, y, np.int64), xs, w)
+    g.ports.append(line(8, prof))
+    g.probes.append(line(12, prof / xs.size))
+    g.probes.append(line(ny - 9, prof / xs.size))
+    return g
+
+
+def waveguide2d_workload(irises: bool = True) -> Workload:
+    """Sec. V-B: pulse of bandwidth 3 GHz (f0 = 2.5 GHz), 20,000 steps; q = 200,
+    five expansion points, M = 1.1, fmax = 3 GHz; reduced at s = 0.99, 4.95,
+    8.91."""
+    return Workload("waveguide2d" + ("" if irises else "_line") + "_f32", waveguide2d(irises), 0.99, 20000,
+                    2.5e9, 3e9, q=200, L=2, M=1.1, fmax=3e9, s_red=[0.99, 4.95, 8.91],
+                    nsteps_red=[20000, 4040, 2244], precision="f32")
+
+
 # ---------------------------------------------------------------- microstrip filter
 def microstrip(seed: int = SEED_BASE + 4, nx: int = 400, ny: int = 200, nz: int = 24,
                dxy: float = 0.4e-3, dz: float = 0.2e-3, n_sub: int = 6) -> GridSpec:

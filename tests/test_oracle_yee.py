@@ -317,3 +317,35 @@ def test_cfl_dt_pinned_to_dispersion_limit():
     assert cfl <= ex and ex / cfl - 1 < 0.5 * (np.pi / (2 * 60)) ** 2
     assert abs(yee.cfl_dt(box(N, d, 4.0)) / cfl - 2.0) < 1e-14
     assert abs(_exact_dt_uniform(N, d, c0 / 2) / ex - 2.0) < 1e-14
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 1, 1e-3, 1.5e-3, 1e-3), (5, 5, 1, 1e-2, 1e-2, 1e-2)])
+def test_single_layer_is_the_2d_tm_problem(dims):
+    """A single layer of cells between the z plates (Sec. V-A/V-B 2-D cases):
+    the live unknowns are Ez, Hx, Hy only, the eigenvalues of the step matrix
+    follow the 2-D Yee dispersion relation (the closed form with m_z = 0), and
+    Eq. (CFL) loses its z term: the exact limit equals the closed form of the
+    highest 2-D mode, above Eq. (CFL) as in 3-D."""
+    nx, ny, nz, a, b, c = dims
+    g = _box(nx, ny, nz, a, b, c)
+    s = yee.assemble(g)
+    assert s.Ne == (nx - 1) * (ny - 1) and s.Nh == (nx - 1) * ny + nx * (ny - 1)
+    assert int(s.e_mask[0].sum()) == 0 and int(s.e_mask[1].sum()) == 0 and int(s.h_mask[2].sum()) == 0
+    dt = 0.99 * yee.cfl_dt(g)
+    ev, ph = _nonstatic_phases(yee.amplification_matrix(s, dt))
+    ref = box_mode_phases(nx, ny, nz, a, b, c, dt)
+    assert np.allclose(np.abs(ev), 1.0, atol=1e-12)
+    assert ph.size == ref.size == (nx - 1) * (ny - 1)
+    assert np.max(np.abs(ph - ref)) < 1e-12
+    exact = max_stable_dt_uniform_box(nx, ny, nz, a, b, c)
+    assert abs(yee.exact_dt_limit(s) / exact - 1) < 1e-9
+    assert yee.cfl_dt(g) <= exact and exact / yee.cfl_dt(g) < 1.25
+
+
+def test_paper_2d_system_sizes():
+    """Table I: N = 30,200 for the 101 x 101 2-D cavity; Sec. V-B: N = 48,440
+    for the 41 x 401 guide (counted without its iris conductors) -- the live
+    Ez, Hx, Hy unknowns of one layer between plates."""
+    for wl, n in ((W.cavity2d_workload(), GOLD["system_sizes_2d"]["cavity"]),
+                  (W.waveguide2d_workload(irises=False), GOLD["system_sizes_2d"]["waveguide"])):
+        assert yee.assemble(wl.grid).N == n
