@@ -5,14 +5,14 @@
 //   e <- Pe e - Qe h + be u^{n+1}
 //   h <- Ph h + Qh e + bh u^{n+1}
 //   y^n = C~ e
-// The two phases depend on each other.  When the step matrices fit one CTA's
-// shared memory (q up to about 90 in FP32) one CTA of 1024 threads runs all
-// steps with a block barrier between phases.  Larger models run on a thread
-// block cluster whose CTAs each hold a slice of rows of the step matrices in
-// shared memory (resident for the whole run); each phase's new state slice is
-// stored into every CTA's copy of the state through distributed shared
-// memory, with one cluster barrier per phase.  Models too large for 16 CTAs
-// stream the matrices from L2 in the one-CTA kernel.
+// The two phases depend on each other.  The model runs on a thread block
+// cluster whose CTAs each hold a slice of rows of the step matrices in shared
+// memory (resident for the whole run); each phase's new state slice is stored
+// into every CTA's copy of the state through distributed shared memory, with
+// one cluster barrier per phase.  Where no cluster can be scheduled, or for
+// models too large for 16 CTAs, one CTA of 1024 threads runs all steps with a
+// block barrier between phases (the matrices in its shared memory when they
+// fit, q up to about 90 in FP32, else streamed from L2).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -203,15 +203,16 @@ static fdtd_status run_t(mor_model *M, int64_t nsteps, const void *u, void *y, i
   const size_t mats = sizeof(T) * ((size_t)q1 * q1 + 2 * (size_t)q1 * q2 + (size_t)q2 * q2 + (size_t)(q1 + q2) * m + (size_t)p * q1);
   const size_t limit = 220 * 1024;
   a.mats_in_smem = vec + mats <= limit;
-  // Cluster form when the matrices exceed one CTA (FDTDMOR_RUN=cta / cluster
-  // forces a form).  The largest schedulable cluster wins: measured at q = 200
-  // (FP32) 7.3, 4.4 and 3.3 us per step with 4, 8 and 16 CTAs (21.8 with one
-  // CTA streaming from L2); FDTDMOR_RUN_CL caps the size.
+  // Cluster form whenever it can be scheduled (FDTDMOR_RUN=cta / cluster
+  // forces a form), the one-CTA form as the fallback.  Measured (FP32, us per
+  // step, one CTA against a cluster of 16): q = 40 3.27 / 2.76, q = 80
+  // 4.61 / 2.89, q = 200 21.3 / 3.33 (clusters of 4 and 8: 7.3, 4.4),
+  // q = 400 46.4 / 5.34; FDTDMOR_RUN_CL caps the size.
   const char *env = getenv("FDTDMOR_RUN");
   const std::string form = env ? env : "";
   const char *envc = getenv("FDTDMOR_RUN_CL");
   const int cl_max = envc ? std::max(2, std::min(16, atoi(envc))) : 16;
-  if ((!a.mats_in_smem && form != "cta") || form == "cluster") {
+  if (form != "cta") {
     auto kern = reduced_run_cluster_kernel<T>;
     for (int cl = cl_max; cl >= 2; cl /= 2) {
       int er = 0, hr = 0;

@@ -340,7 +340,7 @@ def test_reduced_model_matches_oracle_at_bench_settings():
 def test_cluster_reduced_run_matches_oracle(prec, q, tol, tol_cta, monkeypatch):
     """A8, the thread-block-cluster form (row slices of the step matrices
     resident per CTA, state exchanged through distributed shared memory; the
-    default once the matrices exceed one CTA's shared memory, forced here):
+    default at every order where a cluster can be scheduled, forced here):
     steps the GPU-projected model like the one-CTA form in the same precision
     (only the summation order differs) and, in FP64, like the oracle's reduced
     leap-frog on the same matrices, below and above CFL (FP32 stepping of this
