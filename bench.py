@@ -335,6 +335,7 @@ def run_ours(args):
             line["schur_roofline_hbm"] = schur_hbm_measure(F, W, hbm, peak_src)
     if rank == 0 and args.batch:
         line["batch"] = batch_measure(F, W)
+        line["batch"]["reduction"] = batch_reduce_measure(F, W)
     if rank == 0 and args.tensor:
         line["tensor_gram"] = tensor_gram_measure(F, peaks)
         line["precision_study"] = precision_study(F, W)
@@ -395,6 +396,69 @@ def schur_hbm_measure(F, W, hbm, peak_src):
     out = schur_roofline(F, pts, grid, dt0, hbm, peak_src, reps=10, id_bytes=2)
     grid.close()
     return out
+
+
+def batch_reduce_measure(F, W, q_per_port=40, fmax_cav=20e9):
+    """Bases of the batched workload (32 uneven cavities with 1-4 ports and
+    the iris waveguide as one block Krylov of width 2): one
+    mor_build_basis_batched call against one mor_build_basis call per grid,
+    both in FP32 with TF32 CGS2 at tol 1e-4.  Cavities: q = 40 per port,
+    five points, M = 1.1, fmax = 20 GHz (the band of the batch's 10 GHz
+    pulse); waveguide: q = 200, fmax = 45 GHz."""
+    import torch
+    specs = W.cavity_batch()
+    wg = W.waveguide_workload()
+    specs.append(wg.grid)
+    grids = [F.Grid(s, "f32") for s in specs]
+    opts = []
+    for i, g in enumerate(grids):
+        m = len(specs[i].ports)
+        if i == len(grids) - 1:
+            opts.append(dict(q=wg.q, dt0=0.99 * g.cfl_dt(), L=wg.L, M=wg.M, fmax=wg.fmax, tol=1e-4, defl_tol=1e-5))
+        else:
+            opts.append(dict(q=q_per_port * m, dt0=0.99 * g.cfl_dt(), L=2, M=1.1, fmax=fmax_cav, tol=1e-4,
+                             defl_tol=1e-5))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def alone():
+        out = []
+        for g, o in zip(grids, opts):
+            out.append(F.Basis(g, allow_noconv=True, **o))
+        return out
+
+    # warm both paths once on the two smallest grids (kernel loading, pools)
+    small = sorted(range(len(grids)), key=lambda i: specs[i].ncells)[:2]
+    for b in F.build_bases([grids[i] for i in small], [opts[i] for i in small], allow_noconv=True):
+        b.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev[0].record()
+    bb = F.build_bases(grids, opts, allow_noconv=True)
+    ev[1].record()
+    torch.cuda.synchronize()
+    wall_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ev[2].record()
+    ba = alone()
+    ev[3].record()
+    torch.cuda.synchronize()
+    wall_a = time.perf_counter() - t0
+    qs = [(b.info()["q1"], b.info()["q2"]) for b in bb]
+    same = all(qs[i] == (a.info()["q1"], a.info()["q2"]) for i, a in enumerate(ba))
+    worst = max(b.info()["max_resid"] for b in bb)
+    cols = sum(q1 + q2 for q1, q2 in qs)
+    for b in bb + ba:
+        b.close()
+    return {"grids": len(specs), "cells": int(sum(s.ncells for s in specs)),
+            "basis_columns": int(cols), "batched_ms": round(ev[0].elapsed_time(ev[1]), 1),
+            "separate_ms": round(ev[2].elapsed_time(ev[3]), 1), "batched_wall_s": round(wall_b, 3),
+            "separate_wall_s": round(wall_a, 3), "speedup": round(ev[2].elapsed_time(ev[3]) /
+                                                                   ev[0].elapsed_time(ev[1]), 2),
+            "same_orders_as_separate": bool(same), "worst_rel_residual": worst,
+            "workers": int(os.environ.get("FDTDMOR_BATCH_WORKERS", "8")),
+            "opts": {"cavities": f"q = {q_per_port} per port, L = 2, M = 1.1, fmax = {fmax_cav / 1e9:g} GHz",
+                     "waveguide": f"q = {wg.q}, L = {wg.L}, M = {wg.M}, fmax = {wg.fmax / 1e9:g} GHz",
+                     "tol": 1e-4, "orth": "tf32"}}
 
 
 def batch_measure(F, W, nsteps=200):
@@ -735,7 +799,7 @@ def hbm_grid_measure(F, W, hbm, nsteps=200):
             "bytes_per_cell": bytes_per_cell}
 
 
-def reduced_run_measure(F, W, q_list=(200, 400), nsteps=20000):
+def reduced_run_measure(F, W, q_list=(40, 80, 200, 400), nsteps=20000):
     """Reduced leap-frog (mor_run) microseconds per step for FP32 models of
     order q (random SPD-projected models are not needed: the step matrices of
     a real basis of the 64^3 graded cavity at q columns)."""
@@ -873,7 +937,7 @@ def main():
     if args.only_batch:
         from paper_1406_7042_gb300 import fdtdmor as F
         from paper_1406_7042_gb300 import workloads as W
-        print(json.dumps({"only_batch": batch_measure(F, W)}))
+        print(json.dumps({"only_batch": batch_measure(F, W), "reduction": batch_reduce_measure(F, W)}))
         return 0
     if args.impl == "reference":
         return run_reference(args)

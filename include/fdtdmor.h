@@ -392,6 +392,21 @@ FDTD_API fdtd_status mor_basis_info(const mor_basis *basis, int *q1, int *q2, in
 FDTD_API fdtd_status mor_basis_get(const mor_basis *basis, int which, void *dst, fdtd_stream_t stream);
 FDTD_API fdtd_status mor_basis_destroy(mor_basis *basis);
 
+/* A11 -- n bases built together (batching of Sec. IV over uneven grids):
+ * basis i is mor_build_basis(grids[i], &opts[i]) exactly, grid by grid.  The
+ * builds run side by side on streams of the library's own (one per host
+ * worker, at most FDTDMOR_BATCH_WORKERS, default 8), largest grid first,
+ * after the work already queued on `stream`; `stream` then waits for all of
+ * them, and each returned basis belongs to `stream` (mor_basis_destroy
+ * synchronises it).  grids: n distinct grid handles (the same handle twice is
+ * FDTD_EINVAL); opts, out, status: host arrays of n (status may be NULL).
+ * out[i] is NULL where build i failed; status[i] is its status.  Returns
+ * FDTD_OK, else the worst status (a hard error before FDTD_ENOCONV) with the
+ * failing index in fdtd_last_error().  Blocks the calling thread until every
+ * build has finished. */
+FDTD_API fdtd_status mor_build_basis_batched(int n, fdtd_grid *const *grids, const mor_opts *opts,
+                                             fdtd_stream_t stream, mor_basis **out, fdtd_status *status);
+
 /* A6 -- projection, Eq. (R_and_Freduced): D~eps = V1^T D_eps V1,
  * D~se = V1^T D_se V1, D~mu = V2^T D_mu V2, D~sm = V2^T D_sm V2,
  * K~ = V1^T K V2, B~ = V^T B, C~ = C V, accumulated in FP64.  For a basis
@@ -413,9 +428,9 @@ FDTD_API fdtd_status mor_perturb(mor_model *model, double dt, double gamma, int 
 /* A8 -- reduced leap-frog, Eq. (reducedMNAform) in block form, nsteps steps at
  * the dt of the last mor_perturb, in one persistent kernel:
  * e <- Pe e - Qe h + be u^{n+1}, h <- Ph h + Qh e + bh u^{n+1}, y^n = C~ e.
- * Step matrices that fit one CTA's shared memory run on one CTA; larger ones
- * on a thread-block cluster (up to 16 CTAs) holding row slices in shared
- * memory and exchanging the state through distributed shared memory.
+ * It runs on a thread-block cluster (up to 16 CTAs) holding row slices of
+ * the step matrices in shared memory and exchanging the state through
+ * distributed shared memory; where no cluster fits, on one CTA.
  * u: device [nsteps][m], y: device [nsteps][p] (grid type). */
 FDTD_API fdtd_status mor_run(mor_model *model, int64_t nsteps, const void *u, void *y,
                              int reset_state, fdtd_stream_t stream);

@@ -266,16 +266,17 @@ typedef CUresult (*TcEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, v
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static TcEncodeFn tc_encode() {
-  static TcEncodeFn fn = nullptr;
-  if (!fn) {
+  // looked up once (thread-safe static initialisation: batched builds call
+  // this from several host threads)
+  static const TcEncodeFn fn = []() -> TcEncodeFn {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<TcEncodeFn>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<TcEncodeFn>(p);
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 

@@ -132,6 +132,8 @@ _SIGS = [
                                  C.POINTER(C.c_double)]),
     ("mor_basis_get", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("mor_basis_destroy", C.c_int, [C.c_void_p]),
+    ("mor_build_basis_batched", C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(MorOpts), C.c_void_p,
+                                          C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
     ("mor_project", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("mor_perturb", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_int), C.c_void_p]),
     ("mor_run", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -396,6 +398,24 @@ KERNELS = {"auto": 0, "persist": 1, "split": 2, "tma": 3, "fused": 4, "march": 5
 MODEL_FIELDS = {"De": 0, "Dse": 1, "Dm": 2, "Dsm": 3, "K": 4, "Kp": 5, "BE": 6, "CE": 7, "sigma": 8}
 
 
+def _mor_opts(q: int, dt0: float, L: int = 2, M: float = 1.1, fmax: float = 0.0, include_center: bool = True,
+              tol: float = None, maxit: int = 20000, defl_tol: float = None, orth: str = None,
+              solver: str = "auto") -> MorOpts:
+    o = MorOpts()
+    check(lib().mor_opts_default(C.byref(o)))
+    o.q, o.L, o.M, o.fmax, o.dt0 = int(q), int(L), float(M), float(fmax), float(dt0)
+    o.include_center = 1 if include_center else 0
+    if tol is not None:
+        o.tol = float(tol)
+    o.maxit = int(maxit)
+    if defl_tol is not None:
+        o.defl_tol = float(defl_tol)
+    if orth is not None:
+        o.orth = MOR_ORTH[orth]
+    o.solver = MOR_SOLVER[solver]
+    return o
+
+
 class Basis:
     """mor_basis handle: V1 (3nc x q1), V2 (3nc x q2) on the device."""
 
@@ -403,25 +423,16 @@ class Basis:
                  include_center: bool = True, tol: float = None, maxit: int = 20000,
                  defl_tol: float = None, orth: str = None, solver: str = "auto", stream=None,
                  allow_noconv: bool = False):
-        L_ = lib()
-        o = MorOpts()
-        check(L_.mor_opts_default(C.byref(o)))
-        o.q, o.L, o.M, o.fmax, o.dt0 = int(q), int(L), float(M), float(fmax), float(dt0)
-        o.include_center = 1 if include_center else 0
-        if tol is not None:
-            o.tol = float(tol)
-        o.maxit = int(maxit)
-        if defl_tol is not None:
-            o.defl_tol = float(defl_tol)
-        if orth is not None:
-            o.orth = MOR_ORTH[orth]
-        o.solver = MOR_SOLVER[solver]
+        o = _mor_opts(q, dt0, L, M, fmax, include_center, tol, maxit, defl_tol, orth, solver)
         h = C.c_void_p()
-        st = L_.mor_build_basis(grid.h, C.byref(o), _stream_ptr(stream), C.byref(h))
+        st = lib().mor_build_basis(grid.h, C.byref(o), _stream_ptr(stream), C.byref(h))
+        self._adopt(grid, h, st, allow_noconv)
+
+    def _adopt(self, grid, h, st, allow_noconv):
         self.status = st
         if st != FDTD_OK and not (allow_noconv and st == FDTD_ENOCONV and h):
             if h:
-                L_.mor_basis_destroy(h)
+                lib().mor_basis_destroy(h)
             check(st)
         self.h = h
         self.grid = grid
@@ -453,6 +464,32 @@ class Basis:
             self.close()
         except Exception:
             pass
+
+
+def build_bases(grids, opts, stream=None, allow_noconv: bool = False):
+    """Bases of several grids built side by side (mor_build_basis_batched):
+    opts holds one dict of Basis keyword arguments per grid (q and dt0
+    required).  Returns a list of Basis in the order of grids."""
+    n = len(grids)
+    if len(opts) != n:
+        raise ValueError("one opts dict per grid")
+    arr = (MorOpts * n)(*[_mor_opts(**o) for o in opts])
+    hg = (C.c_void_p * n)(*[g.h for g in grids])
+    out = (C.c_void_p * n)()
+    sts = (C.c_int * n)()
+    st = lib().mor_build_basis_batched(n, hg, arr, _stream_ptr(stream), out, sts)
+    if st != FDTD_OK and not (allow_noconv and st == FDTD_ENOCONV):
+        msg = lib().fdtd_last_error().decode(errors="replace")
+        for h in out:
+            if h:
+                lib().mor_basis_destroy(C.c_void_p(h))
+        raise FdtdError(st, msg)
+    res = []
+    for i in range(n):
+        b = Basis.__new__(Basis)
+        b._adopt(grids[i], C.c_void_p(out[i]), sts[i], allow_noconv)
+        res.append(b)
+    return res
 
 
 class Model:

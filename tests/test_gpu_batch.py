@@ -111,3 +111,80 @@ def test_autotune_keeps_results_and_state():
     sys = yee.assemble(s)
     yo, _, _ = yee.Stepper(sys, dt).run(u)
     assert np.max(np.abs(y.cpu().numpy() - yo)) <= 1e-9 * np.abs(yo).max()
+
+
+def _reduce_specs():
+    """Uneven grids for the batched reduction: ragged spacing, lossy and
+    magnetic blocks, one grid of three ports."""
+    out = [ragged_grid(nx=22, ny=15, nz=12, seed=61),
+           ragged_grid(nx=14, ny=18, nz=10, seed=62),
+           ragged_grid(nx=30, ny=11, nz=9, seed=63)]
+    out[1].ports.append(W.Port.point(W.COMP_EZ, 5, 6, 4))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_bases_equal_separate_builds(prec):
+    """mor_build_basis_batched: every basis of the batch is the one its grid
+    builds alone (the builds only run side by side), to rounding, and its
+    projected model the same; the launches of every worker are counted."""
+    specs = _reduce_specs()
+    grids = [F.Grid(s, prec) for s in specs]
+    tol = 1e-10 if prec == "f64" else 1e-5
+    opts = [dict(q=12, dt0=0.99 * g.cfl_dt(), L=1, M=1.1, fmax=60e9, tol=tol) for g in grids]
+    torch.cuda.synchronize()
+    F.launch_count(reset=True)
+    bs = F.build_bases(grids, opts)
+    torch.cuda.synchronize()
+    n_batched = F.launch_count(reset=True)
+    n_alone = 0
+    for g, o, b in zip(grids, opts, bs):
+        a = F.Basis(g, **o)
+        n_alone += F.launch_count(reset=True)
+        assert b.status == a.status == F.FDTD_OK
+        ib, ia = b.info(), a.info()
+        assert (ib["q1"], ib["q2"]) == (ia["q1"], ia["q2"])
+        assert abs(ib["max_resid"] - ia["max_resid"]) <= 0.1 * ia["max_resid"]
+        for which in (1, 2):
+            vb, va = b.V(which), a.V(which)
+            assert float((vb - va).abs().max()) <= (1e-12 if prec == "f64" else 1e-5), which
+        mb, ma = F.Model(g, b), F.Model(g, a)
+        for name in ("De", "Dm", "K", "BE", "CE"):
+            x, y = mb.get(name), ma.get(name)
+            assert np.max(np.abs(x - y)) <= (1e-10 if prec == "f64" else 1e-4) * np.abs(y).max(), name
+    assert n_batched > 0 and abs(n_batched - n_alone) <= 0.1 * n_alone, (n_batched, n_alone)
+
+
+def test_batched_f64_bases_match_the_oracle():
+    """Two small members of a batch, FP64: the batched bases span the oracle's
+    SPRIM bases (sparse-LU chains, CGS2), principal cosines to 1e-8."""
+    from oracle import mor
+    specs = _reduce_specs()[:2]
+    grids = [F.Grid(s, "f64") for s in specs]
+    opts = [dict(q=12, dt0=0.99 * yee.cfl_dt(s), L=1, M=1.1, fmax=60e9, tol=1e-12, defl_tol=1e-6) for s in specs]
+    bs = F.build_bases(grids, opts)
+    for s, o, b in zip(specs, opts, bs):
+        sys = yee.assemble(s)
+        ob = mor.sprim_basis(sys, o["dt0"], o["q"], o["L"], o["M"], o["fmax"], defl_tol=1e-6)
+        for which, comps, Vo in ((1, "E", ob.V1), (2, "H", ob.V2)):
+            V = b.V(which).cpu().numpy()
+            q = V.shape[0]
+            nz, ny, nx = sys.shape
+            A = V.reshape(q, 3, nz, ny, nx)
+            masks = sys.e_mask if comps == "E" else sys.h_mask
+            Vg = np.concatenate([A[:, c][:, masks[c]] for c in range(3)], axis=1).T
+            assert Vg.shape[1] == Vo.shape[1]
+            cosines = np.linalg.svd(Vg.T @ Vo, compute_uv=False)
+            assert cosines.min() > 1 - 1e-8, (which, cosines.min())
+
+
+def test_batched_bases_report_the_failing_member():
+    specs = _reduce_specs()
+    grids = [F.Grid(s, "f32") for s in specs]
+    good = dict(q=8, dt0=0.99 * grids[0].cfl_dt(), L=1, M=1.1, fmax=60e9, tol=1e-4)
+    bad = dict(good, dt0=-1.0)
+    with pytest.raises(F.FdtdError, match="grid 1"):
+        F.build_bases(grids, [good, bad, dict(good, dt0=0.99 * grids[2].cfl_dt())])
+    with pytest.raises(F.FdtdError, match="twice"):
+        F.build_bases([grids[0], grids[0]], [good, good])
+    assert F.build_bases([], []) == []
