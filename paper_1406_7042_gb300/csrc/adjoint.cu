@@ -124,6 +124,8 @@ struct AdjointView {
   DevBuf fsrc, fprb;             // the adjoint run's flat port lists (fused z-march form)
   int nfsrc = 0, nfprb = 0;
   bool fready = false;
+  DevBuf fslot[2], fw[2], fport[2];  // and its folded port maps
+  bool fon[2] = {false, false};
   AdjointView(fdtd_grid *g_, DevBuf *f, int *c, TileLists *l, std::vector<HostPort> *pt, std::vector<HostPort> *pb)
       : g(g_), fields(f), cur(c), lists(l), ports(pt), probes(pb) {
     swap_all();
@@ -132,6 +134,11 @@ struct AdjointView {
     swap_all();
     fsrc.release(g->create_stream);
     fprb.release(g->create_stream);
+    for (int q = 0; q < 2; ++q) {
+      fslot[q].release(g->create_stream);
+      fw[q].release(g->create_stream);
+      fport[q].release(g->create_stream);
+    }
   }
   void swap_all() {
     std::swap(g->flat_src, fsrc);
@@ -139,6 +146,12 @@ struct AdjointView {
     std::swap(g->nflat_src, nfsrc);
     std::swap(g->nflat_prb, nfprb);
     std::swap(g->flat_ready, fready);
+    for (int q = 0; q < 2; ++q) {
+      std::swap(g->fold_slot[q], fslot[q]);
+      std::swap(g->fold_w[q], fw[q]);
+      std::swap(g->fold_port[q], fport[q]);
+      std::swap(g->fold_on[q], fon[q]);
+    }
     std::swap(g->fields[0], fields[0]);
     std::swap(g->fields[1], fields[1]);
     std::swap(g->cur, *cur);

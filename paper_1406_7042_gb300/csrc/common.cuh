@@ -139,6 +139,11 @@ struct fdtd_grid {
   fdtdmor::DevBuf flat_src, flat_prb;  // flat (cell, comp, port, w) lists of the fused z-march form
   int nflat_src = 0, nflat_prb = 0;
   bool flat_ready = false;
+  // sources ([0]) and probes ([1]) folded into the z-march pass: for each
+  // plane that carries any, dense maps of weight (field type) and port
+  // (uint8) by component and cell; fold_slot: int32 [nz], the plane's map or -1
+  fdtdmor::DevBuf fold_slot[2], fold_w[2], fold_port[2];
+  bool fold_on[2] = {false, false};
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
   fdtdmor::DevBuf ecoef;        // per E edge (Ca x3, Cb x3 by cell) for small grids

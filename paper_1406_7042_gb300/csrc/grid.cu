@@ -361,6 +361,11 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->u_graph.release(s);
   g->flat_src.release(s);
   g->flat_prb.release(s);
+  for (int q = 0; q < 2; ++q) {
+    g->fold_slot[q].release(s);
+    g->fold_w[q].release(s);
+    g->fold_port[q].release(s);
+  }
   g->y_graph.release(s);
   for (auto &x : g->ygraph)
     if (x) cudaGraphExecDestroy(x);

@@ -1516,6 +1516,14 @@ struct BasisBuilder {
   // o.maxit caps the inner iterations of one shifted solve (all outer steps).
   static constexpr double kInnerTol = 1e-2;
   static constexpr int kMaxOuter = 8;
+  static double inner_tol() {  // FDTDMOR_INNER_TOL overrides kInnerTol
+    static const double t = [] {
+      const char *e = getenv("FDTDMOR_INNER_TOL");
+      const double v = e ? atof(e) : 0.0;
+      return v > 0 && v < 1 ? v : kInnerTol;
+    }();
+    return t;
+  }
 
   fdtd_status schur_cocg(Work<T> &w, const std::vector<std::complex<double>> &zs) {
     const int nb = (int)zs.size();
@@ -1629,7 +1637,7 @@ struct BasisBuilder {
         c = CgsScal{};
         c.active = need[b];
         c.itol = f64 ? std::min(0.5, 0.5 * o.tol * bn[b] / std::max(rn[b], 1e-300))
-                     : std::max(kInnerTol, std::min(0.5, 0.5 * o.tol * bn[b] / std::max(rn[b], 1e-300)));
+                     : std::max(inner_tol(), std::min(0.5, 0.5 * o.tol * bn[b] / std::max(rn[b], 1e-300)));
         c.imaxit = std::max(1, o.maxit - used[b]);
       }
       FDTD_CHECK_CUDA(cudaMemcpyAsync(sc, hsc.data(), sizeof(CgsScal) * nb, cudaMemcpyHostToDevice, s));
