@@ -124,8 +124,6 @@ struct AdjointView {
   DevBuf fsrc, fprb;             // the adjoint run's flat port lists (fused z-march form)
   int nfsrc = 0, nfprb = 0;
   bool fready = false;
-  DevBuf fslot[2], fw[2], fport[2];  // and its folded port maps
-  bool fon[2] = {false, false};
   AdjointView(fdtd_grid *g_, DevBuf *f, int *c, TileLists *l, std::vector<HostPort> *pt, std::vector<HostPort> *pb)
       : g(g_), fields(f), cur(c), lists(l), ports(pt), probes(pb) {
     swap_all();
@@ -134,11 +132,6 @@ struct AdjointView {
     swap_all();
     fsrc.release(g->create_stream);
     fprb.release(g->create_stream);
-    for (int q = 0; q < 2; ++q) {
-      fslot[q].release(g->create_stream);
-      fw[q].release(g->create_stream);
-      fport[q].release(g->create_stream);
-    }
   }
   void swap_all() {
     std::swap(g->flat_src, fsrc);
@@ -146,12 +139,6 @@ struct AdjointView {
     std::swap(g->nflat_src, nfsrc);
     std::swap(g->nflat_prb, nfprb);
     std::swap(g->flat_ready, fready);
-    for (int q = 0; q < 2; ++q) {
-      std::swap(g->fold_slot[q], fslot[q]);
-      std::swap(g->fold_w[q], fw[q]);
-      std::swap(g->fold_port[q], fport[q]);
-      std::swap(g->fold_on[q], fon[q]);
-    }
     std::swap(g->fields[0], fields[0]);
     std::swap(g->fields[1], fields[1]);
     std::swap(g->cur, *cur);
@@ -292,6 +279,7 @@ extern "C" {
 
 fdtd_status fdtd_adjoint(fdtd_grid *g, double dt, int64_t nsteps, const void *u, const void *dloss_dy,
                          int ncheckpoints, double *grad_eps_cell, double *grad_eps_mat, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g, "fdtd_adjoint: NULL grid");
   FDTD_REQUIRE(dt > 0 && nsteps >= 1, "fdtd_adjoint: need dt > 0 and nsteps >= 1");
   FDTD_REQUIRE(g->ports.empty() || u, "fdtd_adjoint: u is required when the grid has sources");

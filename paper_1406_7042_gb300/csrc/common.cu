@@ -1,6 +1,8 @@
-// Error reporting, allocator hooks and launch accounting of the C ABI.
+// Error reporting, allocator hooks, launch accounting and NVTX ranges of the C ABI.
 #include <cstdarg>
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 
@@ -32,6 +34,22 @@ fdtd_status after_launch(const char *name) {
 }
 
 void add_launches(int64_t n) { g_launches += n; }
+
+static nvtxDomainHandle_t api_domain() {
+  static const nvtxDomainHandle_t d = nvtxDomainCreateA("fdtdmor");  // thread-safe one-time creation
+  return d;
+}
+
+ApiRange::ApiRange(const char *name) {
+  nvtxEventAttributes_t at = {};
+  at.version = NVTX_VERSION;
+  at.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  at.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  at.message.ascii = name;
+  nvtxDomainRangePushEx(api_domain(), &at);
+}
+
+ApiRange::~ApiRange() { nvtxDomainRangePop(api_domain()); }
 
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 256;

@@ -49,6 +49,16 @@ fdtd_status cuda_fail(cudaError_t e, const char *what);
 fdtd_status after_launch(const char *name);
 void add_launches(int64_t n);  // kernel launches made by a graph replay
 
+// NVTX range over one C-ABI call, in the domain "fdtdmor" (a no-op unless a
+// profiler is attached): profiles and traces show which call a kernel ran in.
+struct ApiRange {
+  explicit ApiRange(const char *name);
+  ~ApiRange();
+  ApiRange(const ApiRange &) = delete;
+  ApiRange &operator=(const ApiRange &) = delete;
+};
+#define FDTD_API_RANGE(name) ::fdtdmor::ApiRange fdtd_api_range_(name)
+
 // ------------------------------------------------------------ memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
@@ -139,11 +149,6 @@ struct fdtd_grid {
   fdtdmor::DevBuf flat_src, flat_prb;  // flat (cell, comp, port, w) lists of the fused z-march form
   int nflat_src = 0, nflat_prb = 0;
   bool flat_ready = false;
-  // sources ([0]) and probes ([1]) folded into the z-march pass: for each
-  // plane that carries any, dense maps of weight (field type) and port
-  // (uint8) by component and cell; fold_slot: int32 [nz], the plane's map or -1
-  fdtdmor::DevBuf fold_slot[2], fold_w[2], fold_port[2];
-  bool fold_on[2] = {false, false};
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
   fdtdmor::DevBuf ecoef;        // per E edge (Ca x3, Cb x3 by cell) for small grids

@@ -399,6 +399,7 @@ using namespace fdtdmor;
 extern "C" {
 
 fdtd_status mor_perturb(mor_model *M, double dt, double gamma, int *n_clipped, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(M, "mor_perturb: NULL model");
   FDTD_REQUIRE(dt > 0 && gamma > 0 && gamma <= 1, "mor_perturb: need dt > 0 and 0 < gamma <= 1");
   return perturb_and_prepare(M, dt, gamma, n_clipped, (cudaStream_t)stream);

@@ -196,6 +196,7 @@ extern "C" {
 fdtd_status fdtd_grid_set_materials(fdtd_grid *g, int nmat, const double *eps_r, const double *mu_r,
                                     const double *sig_e, const double *sig_m, const uint8_t *pec,
                                     fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g, "fdtd_grid_set_materials: NULL grid");
   FDTD_REQUIRE(nmat == g->nmat, "fdtd_grid_set_materials: nmat %d differs from the grid's %d", nmat, g->nmat);
   FDTD_REQUIRE(eps_r && mu_r && sig_e && sig_m && pec, "fdtd_grid_set_materials: missing material table");
@@ -230,6 +231,7 @@ fdtd_status fdtd_grid_set_materials(fdtd_grid *g, int nmat, const double *eps_r,
 
 fdtd_status fdtd_grid_create(const fdtd_grid_desc *d, int m, const fdtd_port *ports, int p,
                              const fdtd_port *probes, fdtd_stream_t stream, fdtd_grid **out) {
+  FDTD_API_RANGE(__func__);
   cudaStream_t s = (cudaStream_t)stream;
   FDTD_REQUIRE(d && out, "fdtd_grid_create: NULL descriptor or output");
   *out = nullptr;
@@ -361,11 +363,6 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->u_graph.release(s);
   g->flat_src.release(s);
   g->flat_prb.release(s);
-  for (int q = 0; q < 2; ++q) {
-    g->fold_slot[q].release(s);
-    g->fold_w[q].release(s);
-    g->fold_port[q].release(s);
-  }
   g->y_graph.release(s);
   for (auto &x : g->ygraph)
     if (x) cudaGraphExecDestroy(x);
@@ -396,6 +393,7 @@ fdtd_status fdtd_check(fdtd_grid *g, fdtd_stream_t stream) {
 }
 
 fdtd_status fdtd_fields_get(const fdtd_grid *g, void *fields6, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && fields6, "fdtd_fields_get: NULL argument");
   FDTD_CHECK_CUDA(cudaMemcpyAsync(fields6, g->fields[g->cur].ptr, (size_t)6 * g->nc * g->elem,
                                   cudaMemcpyDefault, (cudaStream_t)stream));
@@ -403,6 +401,7 @@ fdtd_status fdtd_fields_get(const fdtd_grid *g, void *fields6, fdtd_stream_t str
 }
 
 fdtd_status fdtd_planes_get(const fdtd_grid *g, int k0, int nk, void *dst, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && dst, "fdtd_planes_get: NULL argument");
   FDTD_REQUIRE(k0 >= 0 && nk >= 0 && k0 + nk <= g->nz, "fdtd_planes_get: planes [%d, %d) outside 0..%d", k0, k0 + nk,
                g->nz);
@@ -415,6 +414,7 @@ fdtd_status fdtd_planes_get(const fdtd_grid *g, int k0, int nk, void *dst, fdtd_
 }
 
 fdtd_status fdtd_planes_set(fdtd_grid *g, int k0, int nk, const void *src, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && src, "fdtd_planes_set: NULL argument");
   FDTD_REQUIRE(k0 >= 0 && nk >= 0 && k0 + nk <= g->nz, "fdtd_planes_set: planes [%d, %d) outside 0..%d", k0, k0 + nk,
                g->nz);
@@ -428,6 +428,7 @@ fdtd_status fdtd_planes_set(fdtd_grid *g, int k0, int nk, const void *src, fdtd_
 }
 
 fdtd_status fdtd_fields_set(fdtd_grid *g, const void *fields6, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && fields6, "fdtd_fields_set: NULL argument");
   FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fields[g->cur].ptr, fields6, (size_t)6 * g->nc * g->elem,
                                   cudaMemcpyDefault, (cudaStream_t)stream));

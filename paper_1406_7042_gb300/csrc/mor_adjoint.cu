@@ -246,6 +246,7 @@ extern "C" {
 fdtd_status mor_gradient(mor_model *M, const mor_basis *b, fdtd_grid *g, int64_t nsteps, const void *u,
                          const void *dloss_dy, double *grad_eps_cell, double *grad_eps_mat, double *grad_De,
                          fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(M && b && g, "mor_gradient: NULL argument");
   FDTD_REQUIRE(M->perturbed, "mor_gradient: call mor_perturb first (it prepares the step matrices)");
   FDTD_REQUIRE(nsteps >= 1 && (M->m == 0 || u) && (M->p == 0 || dloss_dy), "mor_gradient: bad arguments");

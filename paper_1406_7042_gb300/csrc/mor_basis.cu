@@ -2207,6 +2207,7 @@ fdtd_status mor_opts_default(mor_opts *o) {
 }
 
 fdtd_status mor_build_basis(fdtd_grid *g, const mor_opts *o, fdtd_stream_t stream, mor_basis **out) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && o && out, "mor_build_basis: NULL argument");
   *out = nullptr;
   FDTD_REQUIRE(o->q >= 1 && o->L >= 0 && o->M > 0 && o->dt0 > 0 && o->tol > 0 && o->maxit >= 1,
@@ -2231,6 +2232,7 @@ fdtd_status mor_build_basis(fdtd_grid *g, const mor_opts *o, fdtd_stream_t strea
 
 fdtd_status mor_shifted_solve(fdtd_grid *g, const mor_opts *o, int nb, const double *z, const void *b, void *x,
                               int *iters, double *resid, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && o && z && b && x, "mor_shifted_solve: NULL argument");
   FDTD_REQUIRE(nb >= 1 && nb <= kMaxRhs, "mor_shifted_solve: nb must be 1..%d", kMaxRhs);
   FDTD_REQUIRE(o->dt0 > 0 && o->tol > 0 && o->maxit >= 1, "mor_shifted_solve: need dt0 > 0, tol > 0, maxit >= 1");
@@ -2270,6 +2272,7 @@ fdtd_status fdtd_edge_props_get(fdtd_grid *g, void *dst, fdtd_stream_t stream) {
 
 fdtd_status mor_schur_apply(fdtd_grid *g, double dt0, int nb, const double *z, const void *x, void *y,
                             fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && z && x && y, "mor_schur_apply: NULL argument");
   FDTD_REQUIRE(dt0 > 0, "mor_schur_apply: dt0 must be > 0");
   FDTD_REQUIRE(nb >= 1 && nb <= kMaxRhs, "mor_schur_apply: nb must be 1..%d", kMaxRhs);

@@ -74,6 +74,7 @@ extern "C" {
 
 fdtd_status mor_build_basis_batched(int n, fdtd_grid *const *grids, const mor_opts *opts, fdtd_stream_t stream,
                                     mor_basis **out, fdtd_status *status) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(n >= 0 && (n == 0 || (grids && opts && out)), "mor_build_basis_batched: NULL argument");
   for (int i = 0; i < n; ++i) out[i] = nullptr;
   if (n == 0) return FDTD_OK;
@@ -128,13 +129,13 @@ fdtd_status mor_build_basis_batched(int n, fdtd_grid *const *grids, const mor_op
   // The caller's stream continues after every build.
   fdtd_status st = FDTD_OK;
   for (int w = 0; w < nw; ++w) {
-    cudaEvent_t done;
+    cudaEvent_t done = nullptr;
     if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(done, ws[w]) != cudaSuccess || cudaStreamWaitEvent(cs, done, 0) != cudaSuccess) {
       st = cuda_fail(cudaGetLastError(), "stream join");
       cudaStreamSynchronize(ws[w]);
     }
-    cudaEventDestroy(done);
+    if (done) cudaEventDestroy(done);
   }
   for (int w = 1; w < nw; ++w) add_launches(launches[w]);
 

@@ -328,6 +328,7 @@ extern "C" {
 
 fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, const float *B, int64_t ldb, int N,
                      const float *w, double *G, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(A && B && G, "mor_gram: NULL argument");
   FDTD_REQUIRE(n >= 1 && M >= 0 && N >= 0 && lda >= n && ldb >= n, "mor_gram: bad sizes");
   FDTD_REQUIRE(arith >= MOR_ORTH_NATIVE && arith <= MOR_GRAM_BF16X3, "mor_gram: unknown arithmetic %d", arith);
@@ -361,6 +362,7 @@ fdtd_status mor_gram(int arith, int64_t n, const float *A, int64_t lda, int M, c
 }
 
 fdtd_status mor_project(fdtd_grid *g, const mor_basis *b, fdtd_stream_t stream, mor_model **out) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g && b && out, "mor_project: NULL argument");
   FDTD_REQUIRE(b->prec == g->prec && b->n3 == 3 * g->nc, "mor_project: basis does not belong to this grid");
   *out = nullptr;

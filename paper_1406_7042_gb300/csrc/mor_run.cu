@@ -284,6 +284,7 @@ using namespace fdtdmor;
 extern "C" {
 
 fdtd_status mor_run(mor_model *M, int64_t nsteps, const void *u, void *y, int reset_state, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(M, "mor_run: NULL model");
   FDTD_REQUIRE(M->perturbed, "mor_run: call mor_perturb first (it fixes dt and builds the step matrices)");
   FDTD_REQUIRE(nsteps >= 0, "nsteps must be >= 0");
@@ -327,6 +328,7 @@ fdtd_status mor_model_get(const mor_model *M, int which, double *host_out, int *
 static const char kModelMagic[8] = {'F', 'D', 'T', 'D', 'M', 'O', 'R', '1'};
 
 fdtd_status mor_model_save(const mor_model *M, const char *path, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(M && path, "mor_model_save: NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t hdr[6] = {1, M->q1, M->q2, M->m, M->p, (int32_t)M->prec};
@@ -351,6 +353,7 @@ fdtd_status mor_model_save(const mor_model *M, const char *path, fdtd_stream_t s
 }
 
 fdtd_status mor_model_load(const char *path, fdtd_stream_t stream, mor_model **out) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(path && out, "mor_model_load: NULL argument");
   *out = nullptr;
   FILE *f = fopen(path, "rb");
@@ -413,6 +416,7 @@ fdtd_status mor_model_destroy(mor_model *M) {
 
 fdtd_status mor_compare(const void *y_red, const void *y_ref, int64_t n, int64_t stride, int64_t offset, int p,
                         fdtd_prec prec, double *err, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(y_red && y_ref && err && n >= 1 && stride >= 1 && offset >= 0 && p >= 1, "mor_compare: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf acc;

@@ -84,6 +84,7 @@ extern "C" {
 
 fdtd_status fdtd_dft(const void *y, int64_t nsteps, int p, fdtd_prec prec, double dt, int nf, const double *freqs,
                      int hann, double *out, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(y && freqs && out, "fdtd_dft: NULL argument");
   FDTD_REQUIRE(nsteps >= 1 && p >= 1 && p <= 65535 && nf >= 1 && dt > 0, "fdtd_dft: bad sizes");
   FDTD_REQUIRE(prec == FDTD_F32 || prec == FDTD_F64, "fdtd_dft: prec must be FDTD_F32 or FDTD_F64");
@@ -92,6 +93,7 @@ fdtd_status fdtd_dft(const void *y, int64_t nsteps, int p, fdtd_prec prec, doubl
 
 fdtd_status fdtd_sparams(const void *y, const void *y_inc, int64_t nsteps, int p, fdtd_prec prec, double dt, int nf,
                          const double *freqs, int hann, int port_in, double *out, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(y && y_inc && freqs && out, "fdtd_sparams: NULL argument");
   FDTD_REQUIRE(p >= 1 && port_in >= 0 && port_in < p, "fdtd_sparams: port_in must be in [0, p)");
   FDTD_REQUIRE(nf >= 1, "fdtd_sparams: nf must be >= 1");
@@ -117,6 +119,7 @@ fdtd_status fdtd_sparams(const void *y, const void *y_inc, int64_t nsteps, int p
 fdtd_status fdtd_resonances(const void *y, int64_t nsteps, int p, fdtd_prec prec, double dt, double fmin,
                             double fmax, int nf, int hann, double rel_floor, int npk, double *peaks_hz, int *nfound,
                             fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(peaks_hz && nfound && npk >= 1, "fdtd_resonances: NULL output or npk < 1");
   FDTD_REQUIRE(nf >= 3 && fmax > fmin && fmin >= 0, "fdtd_resonances: need nf >= 3 and 0 <= fmin < fmax");
   std::vector<double> f(nf), Y(2 * (size_t)nf * p);

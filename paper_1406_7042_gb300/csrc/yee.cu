@@ -432,6 +432,7 @@ fdtd_status fdtd_grid_set_kernel(fdtd_grid *g, int kernel) {
 
 fdtd_status fdtd_grid_autotune(fdtd_grid *g, double dt, int trial_steps, int *vw_out, int *lz_out,
                                fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g, "fdtd_grid_autotune: NULL grid");
   FDTD_REQUIRE(dt > 0 && trial_steps >= 1, "fdtd_grid_autotune: need dt > 0 and trial_steps >= 1");
   cudaStream_t s = (cudaStream_t)stream;
@@ -488,6 +489,7 @@ fdtd_status fdtd_grid_autotune(fdtd_grid *g, double dt, int trial_steps, int *vw
 
 fdtd_status fdtd_step(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void *y,
                       int reset_fields, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g, "fdtd_step: NULL grid");
   cudaStream_t s = (cudaStream_t)stream;
   FDTD_CHECK(watchdog_before(g, u, reset_fields, s));
@@ -497,6 +499,7 @@ fdtd_status fdtd_step(fdtd_grid *g, double dt, int64_t nsteps, const void *u, vo
 
 fdtd_status fdtd_step_host(fdtd_grid *g, double dt, int64_t nsteps, const void *u_host,
                            void *y_host, int reset_fields, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(g, "fdtd_step_host: NULL grid");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t ub = (size_t)nsteps * g->ports.size() * g->elem;

@@ -291,6 +291,7 @@ extern "C" {
 
 fdtd_status fdtd_step_batched(fdtd_grid *const *grids, int ngrids, const double *dt, int64_t nsteps,
                               const void *const *u, void *const *y, int reset_fields, fdtd_stream_t stream) {
+  FDTD_API_RANGE(__func__);
   FDTD_REQUIRE(grids && dt && ngrids >= 1, "fdtd_step_batched: need grids, dt and ngrids >= 1");
   FDTD_REQUIRE(nsteps >= 0, "fdtd_step_batched: nsteps must be >= 0");
   return step_batched(grids, ngrids, dt, nsteps, u, y, reset_fields, (cudaStream_t)stream);

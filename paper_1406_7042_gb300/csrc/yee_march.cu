@@ -20,16 +20,10 @@
 //
 // DRAM sees each field value read once and written once per step (the 48 B
 // per cell of the fused form, plus the material map); the halo row's and
-// chunk tops' reads come mostly from L2.  Sources and probes on a few planes
-// are folded into the pass: E^{n+1} = Ca E + Cb (curl H - w u) on a source
-// edge (before H^{n+3/2} reads it), and the owner of a probe edge adds w E^{n+1}
-// to its probe.  Their weights and ports come from dense maps of just those
-// planes.  Otherwise two small kernels apply them afterwards: the step is
-// linear, so a source's effect on this step's H is -Db curlE(dE) on the four H
-// edges around the source edge.
+// chunk tops' reads come mostly from L2.  Sources and probes are applied
+// afterwards by two small kernels: the step is linear, so a source's effect on
+// this step's H is -Db curlE(dE) on the four H edges around the source edge.
 #include <algorithm>
-#include <cstdint>
-#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -92,19 +86,6 @@ struct MarchStage {
   static constexpr size_t SMEM = (size_t)S * BYTES + S * sizeof(uint64_t);
 };
 
-// Folded sources and probes (null pointers: not folded).  slot[k] is plane
-// k's map or -1; map q holds w and port by component c and cell n at
-// (q * 3 + c) * nx * ny + n.
-template <typename T>
-struct MarchFoldArgs {
-  const int32_t *src_slot;
-  const T *src_w;
-  const uint8_t *src_port;
-  const int32_t *prb_slot;
-  const T *prb_w;
-  const uint8_t *prb_port;
-};
-
 // CTAs per SM the register budget is sized for (MTY rows of 32 threads;
 // measured on 384 x 384 x 64: 8 rows beat 16, whose barrier spans twice the warps).
 template <typename T, int VW, int MTY>
@@ -120,7 +101,6 @@ constexpr int march_min_blocks() {
 template <typename T, typename ID, bool HOMOG_H, int VW, int MTY, bool STAGED>
 __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_march_kernel(YeeArgs<T, ID> a, const ID *__restrict__ emat, int lz,
                                                                                             const __grid_constant__ MarchMaps maps,
-                                                                                            const MarchFoldArgs<T> fold,
                                                                                             unsigned *err) {
   constexpr int OWN = MTY - 1;  // rows a CTA owns; the last warp computes E of the next tile's first row
   constexpr int W = LTX * VW;   // cells per tile row
@@ -293,13 +273,6 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
     }
     const T hy_s = __shfl_up_sync(0xffffffffu, hy[VW - 1], 1), hz_s = __shfl_up_sync(0xffffffffu, hz[VW - 1], 1);
     if (tx > 0) { hy_l = hy_s; hz_l = hz_s; }
-    // source term w u of an edge of this plane's map (0 elsewhere)
-    const int ssl = (fold.src_slot && inbox) ? __ldg(fold.src_slot + k) : -1;
-    auto src_term = [&](int c, int64_t cell2) -> T {
-      const int64_t q = ((int64_t)ssl * 3 + c) * plane + cell2;
-      const T w = __ldg(fold.src_w + q);
-      return w != T(0) ? w * __ldg(a.u + fold.src_port[q]) : T(0);
-    };
     // E^{n+1}(k) on the own cells
     T ox[VW], oy[VW], oz[VW];
 #pragma unroll
@@ -329,34 +302,14 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
         if (j == 0 || k == 0) cax = cbx = T(0);
         if (i == 0 || k == 0) cay = cby = T(0);
         if (i == 0 || j == 0) caz = cbz = T(0);
-        T jx = T(0), jy = T(0), jz = T(0);
-        if (ssl >= 0) {
-          const int64_t c2 = (int64_t)j * nx + i;
-          jx = src_term(0, c2);
-          jy = src_term(1, c2);
-          jz = src_term(2, c2);
-        }
-        ox[e] = cax * ex[e] + cbx * ((hz[e] - hz_jm[e]) * ryd - (hy[e] - hy_p[e]) * rzd - jx);
-        oy[e] = cay * ey[e] + cby * ((hx[e] - hx_p[e]) * rzd - (hz[e] - hz_im) * rxd[e] - jy);
-        oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd - jz);
+        ox[e] = cax * ex[e] + cbx * ((hz[e] - hz_jm[e]) * ryd - (hy[e] - hy_p[e]) * rzd);
+        oy[e] = cay * ey[e] + cby * ((hx[e] - hx_p[e]) * rzd - (hz[e] - hz_im) * rxd[e]);
+        oz[e] = caz * ez[e] + cbz * ((hy[e] - hy_im) * rxd[e] - (hx[e] - hx_jm[e]) * ryd);
       }
       if (!top && !halo && ok) {
         stv<VW>(a.Eout + n, ox);
         stv<VW>(a.Eout + nc + n, oy);
         stv<VW>(a.Eout + 2 * nc + n, oz);
-        // probes: the owner of each probe edge of this plane adds w E^{n+1}
-        const int psl = fold.prb_slot ? __ldg(fold.prb_slot + k) : -1;
-        if (psl >= 0) {
-#pragma unroll
-          for (int e = 0; e < VW; ++e) {
-            const T o3[3] = {ox[e], oy[e], oz[e]};
-            for (int c = 0; c < 3; ++c) {
-              const int64_t q = ((int64_t)psl * 3 + c) * plane + (int64_t)j * nx + i0 + e;
-              const T w = __ldg(fold.prb_w + q);
-              if (w != T(0)) atomicAdd(a.y + fold.prb_port[q], w * o3[c]);
-            }
-          }
-        }
       }
     }
     if (halo && tx < OWN) {
@@ -379,14 +332,8 @@ __global__ void __launch_bounds__(LTX *MTY, march_min_blocks<T, VW, MTY>()) yee_
         if (k == 0) ca1 = cb1 = T(0);
         if (jh == 0) ca2 = cb2 = T(0);
         const T rzd = ax(AX_RDD, nx + ny + k);
-        T jyh = T(0), jzh = T(0);
-        if (ssl >= 0) {
-          const int64_t c2 = (int64_t)jh * nx + ih;
-          jyh = src_term(1, c2);
-          jzh = src_term(2, c2);
-        }
-        eyh = ca1 * eyh_o + cb1 * ((hxh - hxh_p) * rzd - (hzh - hzh_m) * rxdh - jyh);
-        ezh = ca2 * ezh_o + cb2 * ((hyh - hyh_m) * rxdh - (hxh - hxh_jm) * rydh - jzh);
+        eyh = ca1 * eyh_o + cb1 * ((hxh - hxh_p) * rzd - (hzh - hzh_m) * rxdh);
+        ezh = ca2 * ezh_o + cb2 * ((hyh - hyh_m) * rxdh - (hxh - hxh_jm) * rydh);
         hxh_p = hxh;
       }
       sh[b][0][tx] = eyh;
@@ -558,11 +505,6 @@ __global__ void yee_march_prb_kernel(YeeArgs<T, ID> a, const FlatPort *__restric
   allow_next_grid();
 }
 
-// Sources or probes on at most this many planes are folded into the pass
-// (their maps cost 3 (elem + 1) bytes per cell of each such plane).
-constexpr int kFoldPlanes = 8;
-constexpr size_t kFoldProbeEntries = 4096;
-
 static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   if (g->flat_ready) return FDTD_OK;
   auto build = [&](const std::vector<HostPort> &ports, DevBuf &buf, int &count) -> fdtd_status {
@@ -579,61 +521,6 @@ static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   };
   FDTD_CHECK(build(g->ports, g->flat_src, g->nflat_src));
   FDTD_CHECK(build(g->probes, g->flat_prb, g->nflat_prb));
-  // Folded forms: ports on at most kFoldPlanes planes, at most 255 of them,
-  // one port per edge; probes only beside folded (or no) sources, since a
-  // probe on a source edge must see the source, and with few entries, each
-  // of which is one atomic per step.
-  const char *fe = getenv("FDTDMOR_MARCH_FOLD");
-  const bool allow = !(fe && atoi(fe) == 0);
-  const int64_t plane = (int64_t)g->nx * g->ny;
-  auto fold = [&](const std::vector<HostPort> &ports, int which, size_t max_entries) -> fdtd_status {
-    g->fold_on[which] = false;
-    if (!allow || ports.empty() || ports.size() > 255) return FDTD_OK;
-    std::vector<int32_t> slot(g->nz, -1);
-    int nmaps = 0;
-    size_t entries = 0;
-    for (const HostPort &hp : ports)
-      for (int64_t cell : hp.cell) {
-        const int k = (int)(cell / plane);
-        if (slot[k] < 0) slot[k] = nmaps++;
-        ++entries;
-      }
-    if (nmaps > kFoldPlanes || entries > max_entries) return FDTD_OK;
-    const size_t len = (size_t)nmaps * 3 * plane;
-    std::vector<double> w(len, 0.0);
-    std::vector<int> port(len, -1);
-    for (size_t pi = 0; pi < ports.size(); ++pi) {
-      const HostPort &hp = ports[pi];
-      for (size_t e = 0; e < hp.cell.size(); ++e) {
-        const int64_t cell = hp.cell[e];
-        const size_t q = ((size_t)slot[cell / plane] * 3 + hp.comp) * plane + (size_t)(cell % plane);
-        if (port[q] >= 0 && port[q] != (int)pi) return FDTD_OK;  // two ports on one edge
-        port[q] = (int)pi;
-        w[q] += hp.w[e];
-      }
-    }
-    std::vector<uint8_t> p8(len, 0);
-    for (size_t q = 0; q < len; ++q) p8[q] = port[q] < 0 ? 0 : (uint8_t)port[q];
-    FDTD_CHECK(g->fold_slot[which].alloc(sizeof(int32_t) * g->nz, s));
-    FDTD_CHECK(g->fold_w[which].alloc(len * g->elem, s));
-    FDTD_CHECK(g->fold_port[which].alloc(len, s));
-    FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fold_slot[which].ptr, slot.data(), sizeof(int32_t) * g->nz,
-                                    cudaMemcpyHostToDevice, s));
-    if (g->prec == FDTD_F64) {
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fold_w[which].ptr, w.data(), len * 8, cudaMemcpyHostToDevice, s));
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fold_port[which].ptr, p8.data(), len, cudaMemcpyHostToDevice, s));
-      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
-    } else {
-      std::vector<float> wf(w.begin(), w.end());
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fold_w[which].ptr, wf.data(), len * 4, cudaMemcpyHostToDevice, s));
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fold_port[which].ptr, p8.data(), len, cudaMemcpyHostToDevice, s));
-      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
-    }
-    g->fold_on[which] = true;
-    return FDTD_OK;
-  };
-  FDTD_CHECK(fold(g->ports, 0, SIZE_MAX));
-  if (g->ports.empty() || g->fold_on[0]) FDTD_CHECK(fold(g->probes, 1, kFoldProbeEntries));
   g->flat_ready = true;
   return FDTD_OK;
 }
@@ -698,18 +585,7 @@ static fdtd_status launch_march_main(fdtd_grid *g, const YeeArgs<T, ID> &a, cuda
   memset(&none_maps, 0, sizeof(none_maps));
   const MarchMaps *mp = &none_maps;
   if (STAGED) FDTD_CHECK(march_maps<ID>(g, &mp));
-  MarchFoldArgs<T> fa = {};
-  if (g->fold_on[0]) {
-    fa.src_slot = g->fold_slot[0].as<const int32_t>();
-    fa.src_w = g->fold_w[0].as<const T>();
-    fa.src_port = g->fold_port[0].as<const uint8_t>();
-  }
-  if (g->fold_on[1]) {
-    fa.prb_slot = g->fold_slot[1].as<const int32_t>();
-    fa.prb_w = g->fold_w[1].as<const T>();
-    fa.prb_port = g->fold_port[1].as<const uint8_t>();
-  }
-  FDTD_CHECK_CUDA(launch_dependent_smem(kern, grid, dim3(LTX, MTY), smem, s, a, g->emat.as<ID>(), lz, *mp, fa,
+  FDTD_CHECK_CUDA(launch_dependent_smem(kern, grid, dim3(LTX, MTY), smem, s, a, g->emat.as<ID>(), lz, *mp,
                                         g->errflag.as<unsigned>()));
   return FDTD_OK;
 }
@@ -728,12 +604,12 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
     FDTD_CHECK((launch_march_main<T, ID, HH, VW, MTY, false>(g, a, s)));
   }
   FDTD_CHECK(after_launch("yee_march_kernel"));
-  if (g->nflat_src && !g->fold_on[0]) {
+  if (g->nflat_src) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_src_kernel<T, ID, HH>, dim3((g->nflat_src + 127) / 128), dim3(128), s, a,
                                      g->flat_src.as<const FlatPort>(), g->nflat_src));
     FDTD_CHECK(after_launch("yee_march_src_kernel"));
   }
-  if (g->nflat_prb && !g->fold_on[1]) {
+  if (g->nflat_prb) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_prb_kernel<T, ID>, dim3((g->nflat_prb + 127) / 128), dim3(128), s, a,
                                      g->flat_prb.as<const FlatPort>(), g->nflat_prb));
     FDTD_CHECK(after_launch("yee_march_prb_kernel"));
