@@ -124,6 +124,10 @@ struct AdjointView {
   DevBuf fsrc, fprb;             // the adjoint run's flat port lists (fused z-march form)
   int nfsrc = 0, nfprb = 0;
   bool fready = false;
+  DevBuf xoff, xfac, xport;      // and its gathered source terms
+  int nx_ = 0;
+  int64_t xver = -1;
+  bool xone = false;
   AdjointView(fdtd_grid *g_, DevBuf *f, int *c, TileLists *l, std::vector<HostPort> *pt, std::vector<HostPort> *pb)
       : g(g_), fields(f), cur(c), lists(l), ports(pt), probes(pb) {
     swap_all();
@@ -132,6 +136,9 @@ struct AdjointView {
     swap_all();
     fsrc.release(g->create_stream);
     fprb.release(g->create_stream);
+    xoff.release(g->create_stream);
+    xfac.release(g->create_stream);
+    xport.release(g->create_stream);
   }
   void swap_all() {
     std::swap(g->flat_src, fsrc);
@@ -139,6 +146,12 @@ struct AdjointView {
     std::swap(g->nflat_src, nfsrc);
     std::swap(g->nflat_prb, nfprb);
     std::swap(g->flat_ready, fready);
+    std::swap(g->fix_off, xoff);
+    std::swap(g->fix_fac, xfac);
+    std::swap(g->fix_port, xport);
+    std::swap(g->nfix, nx_);
+    std::swap(g->fix_version, xver);
+    std::swap(g->fix_one, xone);
     std::swap(g->fields[0], fields[0]);
     std::swap(g->fields[1], fields[1]);
     std::swap(g->cur, *cur);

@@ -149,6 +149,13 @@ struct fdtd_grid {
   fdtdmor::DevBuf flat_src, flat_prb;  // flat (cell, comp, port, w) lists of the fused z-march form
   int nflat_src = 0, nflat_prb = 0;
   bool flat_ready = false;
+  // the sources' terms gathered per (field value, port) for the coefficients
+  // of ctab_version fix_version (z-march form); fix_one: sources and probes
+  // in one launch (no probe edge carries a source term)
+  fdtdmor::DevBuf fix_off, fix_fac, fix_port;
+  int nfix = 0;
+  int64_t fix_version = -1;
+  bool fix_one = false;
   fdtdmor::DevBuf emat;         // per cell: material of its uniform E neighbourhood, or ~0
   bool emat_ready = false;
   fdtdmor::DevBuf ecoef;        // per E edge (Ca x3, Cb x3 by cell) for small grids

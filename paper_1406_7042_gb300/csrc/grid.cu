@@ -363,6 +363,9 @@ fdtd_status fdtd_grid_destroy(fdtd_grid *g) {
   g->u_graph.release(s);
   g->flat_src.release(s);
   g->flat_prb.release(s);
+  g->fix_off.release(s);
+  g->fix_fac.release(s);
+  g->fix_port.release(s);
   g->y_graph.release(s);
   for (auto &x : g->ygraph)
     if (x) cudaGraphExecDestroy(x);

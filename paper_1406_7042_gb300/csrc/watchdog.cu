@@ -13,7 +13,9 @@
 // density over eps0) stays within the ratio of the largest to the smallest
 // relative material constant of it.  fdtd_check reports
 // either bit as FDTD_EUNSTABLE; in synchronous mode fdtd_step itself returns it.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "common.cuh"
 #include "grid_internal.cuh"
@@ -21,23 +23,42 @@
 namespace fdtdmor {
 
 // sum of E^2 + eta0^2 H^2 over the six arrays (the vacuum field energy over
-// eps0 per unit volume; E arrays first, H arrays from n/2 on)
+// eps0 per unit volume): blockIdx.y = 0 sums the three E arrays, 1 the three
+// H arrays.  Each thread sums its values in the field type (FP32 grids: float4
+// loads, a few hundred values per thread, finite for values below 1e19) and
+// the block totals go to FP64; FP64 arithmetic on every value would make this
+// pass FP64-throughput-bound instead of memory-bound.
 template <typename T>
-__global__ void field_energy_kernel(const T *__restrict__ f, int64_t n, double *__restrict__ out) {
+__global__ void field_energy_kernel(const T *__restrict__ f, int64_t half, double *__restrict__ out) {
   __shared__ double sh[32];
   const double eta2 = kMu0 / kEps0;
-  double acc = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)f[i];
-    acc += (2 * i < n ? 1.0 : eta2) * v * v;
+  const T *p = f + blockIdx.y * half;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  T acc = T(0);
+  int64_t done = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (((uintptr_t)p & 15) == 0) {
+      const float4 *p4 = reinterpret_cast<const float4 *>(p);
+      const int64_t n4 = half / 4;
+      for (int64_t i = t0; i < n4; i += stride) {
+        const float4 v = __ldg(p4 + i);
+        acc += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+      }
+      done = 4 * n4;
+    }
   }
-  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  for (int64_t i = done + t0; i < half; i += stride) {
+    const T v = p[i];
+    acc += v * v;
+  }
+  double d = (double)acc;
+  for (int o = 16; o; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    atomicAdd(out, t);
+    atomicAdd(out, (blockIdx.y ? eta2 : 1.0) * t);
   }
 }
 
@@ -48,12 +69,12 @@ __global__ void watchdog_judge_kernel(const double *__restrict__ acc, double gro
 }
 
 static fdtd_status field_energy(fdtd_grid *g, double *slot, cudaStream_t s) {
-  const int64_t n = 6 * g->nc;
-  const int blocks = (int)std::min<int64_t>(152 * 4, (n + 255) / 256);
+  const int64_t half = 3 * g->nc;
+  const dim3 blocks((unsigned)std::min<int64_t>(152 * 4, (half + 1023) / 1024), 2);
   if (g->prec == FDTD_F64)
-    field_energy_kernel<double><<<blocks, 256, 0, s>>>(g->fields[g->cur].as<double>(), n, slot);
+    field_energy_kernel<double><<<blocks, 256, 0, s>>>(g->fields[g->cur].as<double>(), half, slot);
   else
-    field_energy_kernel<float><<<blocks, 256, 0, s>>>(g->fields[g->cur].as<float>(), n, slot);
+    field_energy_kernel<float><<<blocks, 256, 0, s>>>(g->fields[g->cur].as<float>(), half, slot);
   return after_launch("field_energy_kernel");
 }
 

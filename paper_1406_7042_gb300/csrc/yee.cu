@@ -290,7 +290,7 @@ static fdtd_status step_graph(fdtd_grid *g, int kind, int kchunk, cudaStream_t s
                       (uint64_t)g->homog_h,
                       (uint64_t)kchunk,
                       dtbits,
-                      (uint64_t)(uintptr_t)g->ctab.ptr,
+                      (uint64_t)(uintptr_t)g->ctab.ptr ^ ((uint64_t)g->ctab_version << 40),  // tables built from it
                       (uint64_t)(uintptr_t)g->lists.src_ptr.ptr,
                       (uint64_t)(uintptr_t)g->lists.prb_ptr.ptr,
                       (uint64_t)(uintptr_t)g->emat.ptr ^ ((uint64_t)(uintptr_t)g->ecoef.ptr << 1),

@@ -428,67 +428,109 @@ struct FlatPort {
   double w;
 };
 
+// The terms of source entry f, per unit of its port's u: dE = -Cb w on its E
+// edge, then -Db (curlE dE) on each H edge whose curl contains that edge.
+// emit(offset from the E base of the field buffer, factor).
+template <typename T, typename ID, bool HOMOG_H, typename Emit>
+__device__ __forceinline__ void src_terms(const YeeArgs<T, ID> &a, const FlatPort &f, Emit emit) {
+  const int nx = a.nx, ny = a.ny, ntot = nx + ny + a.nz;
+  const int64_t nc = a.nc, plane = (int64_t)nx * ny, n = f.cell;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / plane);
+  auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
+  const ID *M = a.mat;
+  T ca, cb = 0;
+  const int c = f.comp;
+  if (c == 0 && j > 0 && k > 0)
+    e_coef(a, M[n - nx - plane], M[n - plane], M[n - nx], M[n], ax(AX_WLO, nx + j), ax(AX_WHI, nx + j),
+           ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+  else if (c == 1 && i > 0 && k > 0)
+    e_coef(a, M[n - 1 - plane], M[n - plane], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i),
+           ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
+  else if (c == 2 && i > 0 && j > 0)
+    e_coef(a, M[n - 1 - nx], M[n - nx], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i), ax(AX_WLO, nx + j),
+           ax(AX_WHI, nx + j), ca, cb);
+  const T dE = -cb * (T)f.w;
+  if (dE == T(0)) return;
+  emit(c * nc + n, dE);
+  // Db of H component hc at cell (ii, jj, kk), 0 where the update forces H to 0
+  auto dbh = [&](int hc, int ii, int jj, int kk) -> T {
+    if (ii < 0 || jj < 0 || kk < 0) return T(0);
+    if ((hc == 0 && ii == 0) || (hc == 1 && jj == 0) || (hc == 2 && kk == 0)) return T(0);
+    T da = __ldg(a.ctab + 2 * a.nmat), db = __ldg(a.ctab + 3 * a.nmat);
+    if (!HOMOG_H) {
+      const int64_t cc = kk * plane + (int64_t)jj * nx + ii;
+      const int idx = hc == 0 ? ii : (hc == 1 ? nx + jj : nx + ny + kk);
+      const int64_t lo = hc == 0 ? cc - 1 : (hc == 1 ? cc - nx : cc - plane);
+      h_coef(a, M[lo], M[cc], ax(AX_WLO, idx), ax(AX_WHI, idx), da, db);
+    }
+    return db;
+  };
+  auto addh = [&](int hc, int ii, int jj, int kk, T coef) {
+    const T db = dbh(hc, ii, jj, kk);
+    if (db != T(0)) emit(3 * nc + hc * nc + kk * plane + (int64_t)jj * nx + ii, -db * coef * dE);
+  };
+  // (curl E)_hc at an H edge = sum of +-(1/d) E over its face; the terms of this E edge:
+  if (c == 0) {         // Ex(i,j,k): Hy(i,j,k) -1/dz_k, Hy(i,j,k-1) +1/dz_{k-1}, Hz(i,j,k) +1/dy_j, Hz(i,j-1,k) -1/dy_{j-1}
+    addh(1, i, j, k, -ax(AX_RD, nx + ny + k));
+    if (k > 0) addh(1, i, j, k - 1, ax(AX_RD, nx + ny + k - 1));
+    addh(2, i, j, k, ax(AX_RD, nx + j));
+    if (j > 0) addh(2, i, j - 1, k, -ax(AX_RD, nx + j - 1));
+  } else if (c == 1) {  // Ey(i,j,k): Hz(i,j,k) -1/dx_i, Hz(i-1,j,k) +1/dx_{i-1}, Hx(i,j,k) +1/dz_k, Hx(i,j,k-1) -1/dz_{k-1}
+    addh(2, i, j, k, -ax(AX_RD, i));
+    if (i > 0) addh(2, i - 1, j, k, ax(AX_RD, i - 1));
+    addh(0, i, j, k, ax(AX_RD, nx + ny + k));
+    if (k > 0) addh(0, i, j, k - 1, -ax(AX_RD, nx + ny + k - 1));
+  } else {              // Ez(i,j,k): Hx(i,j,k) -1/dy_j, Hx(i,j-1,k) +1/dy_{j-1}, Hy(i,j,k) +1/dx_i, Hy(i-1,j,k) -1/dx_{i-1}
+    addh(0, i, j, k, -ax(AX_RD, nx + j));
+    if (j > 0) addh(0, i, j - 1, k, ax(AX_RD, nx + j - 1));
+    addh(1, i, j, k, ax(AX_RD, i));
+    if (i > 0) addh(1, i - 1, j, k, -ax(AX_RD, i - 1));
+  }
+}
+
 template <typename T, typename ID, bool HOMOG_H>
 __global__ void yee_march_src_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ src, int nsrc) {
   wait_prior_grid();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < nsrc) {
     const FlatPort f = src[q];
-    const int nx = a.nx, ny = a.ny, nz = a.nz, ntot = nx + ny + nz;
-    const int64_t nc = a.nc, plane = (int64_t)nx * ny, n = f.cell;
-    const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / plane);
-    auto ax = [&](int table, int idx) { return __ldg(a.ax + table * ntot + idx); };
-    const ID *M = a.mat;
-    T ca, cb = 0;
-    const int c = f.comp;
-    if (c == 0 && j > 0 && k > 0)
-      e_coef(a, M[n - nx - plane], M[n - plane], M[n - nx], M[n], ax(AX_WLO, nx + j), ax(AX_WHI, nx + j),
-             ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
-    else if (c == 1 && i > 0 && k > 0)
-      e_coef(a, M[n - 1 - plane], M[n - plane], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i),
-             ax(AX_WLO, nx + ny + k), ax(AX_WHI, nx + ny + k), ca, cb);
-    else if (c == 2 && i > 0 && j > 0)
-      e_coef(a, M[n - 1 - nx], M[n - nx], M[n - 1], M[n], ax(AX_WLO, i), ax(AX_WHI, i), ax(AX_WLO, nx + j),
-             ax(AX_WHI, nx + j), ca, cb);
-    const T dE = -cb * (T)f.w * a.u[f.port];
-    if (dE != T(0)) {
-      atomicAdd(&a.Eout[c * nc + n], dE);
-      // Db of H component hc at cell (ii, jj, kk), 0 where the update forces H to 0
-      auto dbh = [&](int hc, int ii, int jj, int kk) -> T {
-        if (ii < 0 || jj < 0 || kk < 0) return T(0);
-        if ((hc == 0 && ii == 0) || (hc == 1 && jj == 0) || (hc == 2 && kk == 0)) return T(0);
-        T da = __ldg(a.ctab + 2 * a.nmat), db = __ldg(a.ctab + 3 * a.nmat);
-        if (!HOMOG_H) {
-          const int64_t cc = kk * plane + (int64_t)jj * nx + ii;
-          const int idx = hc == 0 ? ii : (hc == 1 ? nx + jj : nx + ny + kk);
-          const int64_t lo = hc == 0 ? cc - 1 : (hc == 1 ? cc - nx : cc - plane);
-          h_coef(a, M[lo], M[cc], ax(AX_WLO, idx), ax(AX_WHI, idx), da, db);
-        }
-        return db;
-      };
-      auto addh = [&](int hc, int ii, int jj, int kk, T coef) {
-        const T db = dbh(hc, ii, jj, kk);
-        if (db != T(0)) atomicAdd(&a.Hout[hc * nc + kk * plane + (int64_t)jj * nx + ii], -db * coef * dE);
-      };
-      // (curl E)_hc at an H edge = sum of +-(1/d) E over its face; the terms of this E edge:
-      if (c == 0) {         // Ex(i,j,k): Hy(i,j,k) -1/dz_k, Hy(i,j,k-1) +1/dz_{k-1}, Hz(i,j,k) +1/dy_j, Hz(i,j-1,k) -1/dy_{j-1}
-        addh(1, i, j, k, -ax(AX_RD, nx + ny + k));
-        if (k > 0) addh(1, i, j, k - 1, ax(AX_RD, nx + ny + k - 1));
-        addh(2, i, j, k, ax(AX_RD, nx + j));
-        if (j > 0) addh(2, i, j - 1, k, -ax(AX_RD, nx + j - 1));
-      } else if (c == 1) {  // Ey(i,j,k): Hz(i,j,k) -1/dx_i, Hz(i-1,j,k) +1/dx_{i-1}, Hx(i,j,k) +1/dz_k, Hx(i,j,k-1) -1/dz_{k-1}
-        addh(2, i, j, k, -ax(AX_RD, i));
-        if (i > 0) addh(2, i - 1, j, k, ax(AX_RD, i - 1));
-        addh(0, i, j, k, ax(AX_RD, nx + ny + k));
-        if (k > 0) addh(0, i, j, k - 1, -ax(AX_RD, nx + ny + k - 1));
-      } else {              // Ez(i,j,k): Hx(i,j,k) -1/dy_j, Hx(i,j-1,k) +1/dy_{j-1}, Hy(i,j,k) +1/dx_i, Hy(i-1,j,k) -1/dx_{i-1}
-        addh(0, i, j, k, -ax(AX_RD, nx + j));
-        if (j > 0) addh(0, i, j - 1, k, ax(AX_RD, nx + j - 1));
-        addh(1, i, j, k, ax(AX_RD, i));
-        if (i > 0) addh(1, i - 1, j, k, -ax(AX_RD, i - 1));
-      }
-      (void)nz;
-    }
+    const T u = a.u[f.port];
+    src_terms<T, ID, HOMOG_H>(a, f, [&](int64_t off, T fac) { atomicAdd(a.Eout + off, fac * u); });
+  }
+  allow_next_grid();
+}
+
+// Source terms of every entry for the current coefficients (at most five per
+// entry; unused slots get offset -1), gathered on the host into one term per
+// (field value, port).
+template <typename T, typename ID, bool HOMOG_H>
+__global__ void yee_march_src_terms_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ src, int nsrc,
+                                           int64_t *__restrict__ off, T *__restrict__ fac) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsrc) return;
+  int used = 0;
+  src_terms<T, ID, HOMOG_H>(a, src[q], [&](int64_t o, T v) {
+    if (used < 5) { off[5 * (int64_t)q + used] = o; fac[5 * (int64_t)q + used] = v; ++used; }
+  });
+  for (; used < 5; ++used) off[5 * (int64_t)q + used] = -1;
+}
+
+// Sources and probes of one step in one launch, after the fused pass: thread
+// t < nterm adds its term (one per field value and port, so no two threads
+// write the same value) times u; the others read a probe entry's E^{n+1}
+// (no probe edge carries a source term, checked when the terms were built).
+template <typename T, typename ID>
+__global__ void yee_march_fix_kernel(YeeArgs<T, ID> a, const int64_t *__restrict__ off, const T *__restrict__ fac,
+                                     const int32_t *__restrict__ port, int nterm, const FlatPort *__restrict__ prb,
+                                     int nprb) {
+  wait_prior_grid();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nterm) {
+    T *f = a.Eout + off[t];
+    *f += fac[t] * a.u[port[t]];
+  } else if (t - nterm < nprb) {
+    const FlatPort pe = prb[t - nterm];
+    atomicAdd(&a.y[pe.port], (T)pe.w * a.Eout[pe.comp * a.nc + pe.cell]);
   }
   allow_next_grid();
 }
@@ -522,6 +564,81 @@ static fdtd_status ensure_flat(fdtd_grid *g, cudaStream_t s) {
   FDTD_CHECK(build(g->ports, g->flat_src, g->nflat_src));
   FDTD_CHECK(build(g->probes, g->flat_prb, g->nflat_prb));
   g->flat_ready = true;
+  return FDTD_OK;
+}
+
+// Gathers the sources' terms for the current coefficients (outside any graph
+// capture: the first step of a run is launched directly): one term per field
+// value and port, so the per-step kernel needs no atomics, and a check that no
+// probe edge carries a term, so probes can share its launch.
+template <typename T, typename ID, bool HH>
+static fdtd_status ensure_fix(fdtd_grid *g, const YeeArgs<T, ID> &a, cudaStream_t s) {
+  if (g->fix_version == g->ctab_version) return FDTD_OK;
+  g->fix_one = false;
+  g->nfix = 0;
+  if (g->nflat_src) {
+    const int n = g->nflat_src;
+    DevBuf doff, dfac;
+    struct Rel {
+      DevBuf *a, *b;
+      cudaStream_t s;
+      ~Rel() { a->release(s); b->release(s); }
+    } rel{&doff, &dfac, s};
+    FDTD_CHECK(doff.alloc((size_t)5 * n * sizeof(int64_t), s));
+    FDTD_CHECK(dfac.alloc((size_t)5 * n * sizeof(T), s));
+    yee_march_src_terms_kernel<T, ID, HH><<<(n + 127) / 128, 128, 0, s>>>(a, g->flat_src.as<const FlatPort>(), n,
+                                                                       doff.as<int64_t>(), dfac.as<T>());
+    FDTD_CHECK(after_launch("yee_march_src_terms_kernel"));
+    std::vector<int64_t> off((size_t)5 * n);
+    std::vector<T> fac((size_t)5 * n);
+    std::vector<FlatPort> src(n);
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(off.data(), doff.ptr, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(fac.data(), dfac.ptr, fac.size() * sizeof(T), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaMemcpyAsync(src.data(), g->flat_src.ptr, n * sizeof(FlatPort), cudaMemcpyDeviceToHost, s));
+    FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+    struct Term {
+      int64_t off;
+      int port;
+      T fac;
+    };
+    std::vector<Term> t;
+    t.reserve(off.size());
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < 5; ++r)
+        if (off[5 * (size_t)q + r] >= 0) t.push_back(Term{off[5 * (size_t)q + r], src[q].port, fac[5 * (size_t)q + r]});
+    std::sort(t.begin(), t.end(), [](const Term &x, const Term &y) { return x.off != y.off ? x.off < y.off : x.port < y.port; });
+    std::vector<int64_t> uo;
+    std::vector<T> uf;
+    std::vector<int32_t> up;
+    for (size_t q = 0; q < t.size(); ++q) {
+      if (!uo.empty() && uo.back() == t[q].off && up.back() == t[q].port) uf.back() += t[q].fac;
+      else { uo.push_back(t[q].off); uf.push_back(t[q].fac); up.push_back(t[q].port); }
+    }
+    // one writer per field value: the same value under two ports would race
+    bool unique = true;
+    for (size_t q = 1; q < uo.size(); ++q) unique &= uo[q] != uo[q - 1];
+    bool disjoint = true;
+    if (g->nflat_prb) {
+      std::vector<FlatPort> prb(g->nflat_prb);
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(prb.data(), g->flat_prb.ptr, prb.size() * sizeof(FlatPort),
+                                      cudaMemcpyDeviceToHost, s));
+      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+      for (const FlatPort &pe : prb)
+        disjoint &= !std::binary_search(uo.begin(), uo.end(), pe.comp * g->nc + pe.cell);
+    }
+    if (unique && !uo.empty()) {
+      g->nfix = (int)uo.size();
+      FDTD_CHECK(g->fix_off.alloc(uo.size() * sizeof(int64_t), s));
+      FDTD_CHECK(g->fix_fac.alloc(uf.size() * sizeof(T), s));
+      FDTD_CHECK(g->fix_port.alloc(up.size() * sizeof(int32_t), s));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_off.ptr, uo.data(), uo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_fac.ptr, uf.data(), uf.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_port.ptr, up.data(), up.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
+      g->fix_one = disjoint;
+    }
+  }
+  g->fix_version = g->ctab_version;
   return FDTD_OK;
 }
 
@@ -595,6 +712,7 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
   FDTD_CHECK(ensure_emat<ID>(g, s));
   FDTD_CHECK(ensure_flat(g, s));
   YeeArgs<T, ID> a = split_args<T, ID>(g);
+  FDTD_CHECK((ensure_fix<T, ID, HH>(g, a, s)));
   a.u = static_cast<const T *>(u_row);
   a.y = static_cast<T *>(y_row);
   if constexpr (sizeof(T) == 4 && VW == 4 && MTY == 8) {
@@ -604,7 +722,21 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
     FDTD_CHECK((launch_march_main<T, ID, HH, VW, MTY, false>(g, a, s)));
   }
   FDTD_CHECK(after_launch("yee_march_kernel"));
-  if (g->nflat_src) {
+  if (g->nfix && g->fix_one) {  // gathered source terms and the probes in one launch
+    const int nt = g->nfix + g->nflat_prb;
+    FDTD_CHECK_CUDA(launch_dependent(yee_march_fix_kernel<T, ID>, dim3((nt + 255) / 256), dim3(256), s, a,
+                                     g->fix_off.as<const int64_t>(), g->fix_fac.as<const T>(),
+                                     g->fix_port.as<const int32_t>(), g->nfix, g->flat_prb.as<const FlatPort>(),
+                                     g->nflat_prb));
+    FDTD_CHECK(after_launch("yee_march_fix_kernel"));
+    return FDTD_OK;
+  }
+  if (g->nfix) {
+    FDTD_CHECK_CUDA(launch_dependent(yee_march_fix_kernel<T, ID>, dim3((g->nfix + 255) / 256), dim3(256), s, a,
+                                     g->fix_off.as<const int64_t>(), g->fix_fac.as<const T>(),
+                                     g->fix_port.as<const int32_t>(), g->nfix, g->flat_prb.as<const FlatPort>(), 0));
+    FDTD_CHECK(after_launch("yee_march_fix_kernel"));
+  } else if (g->nflat_src) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_src_kernel<T, ID, HH>, dim3((g->nflat_src + 127) / 128), dim3(128), s, a,
                                      g->flat_src.as<const FlatPort>(), g->nflat_src));
     FDTD_CHECK(after_launch("yee_march_src_kernel"));
