@@ -520,14 +520,14 @@ __global__ void yee_march_src_terms_kernel(YeeArgs<T, ID> a, const FlatPort *__r
 // write the same value) times u; the others read a probe entry's E^{n+1}
 // (no probe edge carries a source term, checked when the terms were built).
 template <typename T, typename ID>
-__global__ void yee_march_fix_kernel(YeeArgs<T, ID> a, const int64_t *__restrict__ off, const T *__restrict__ fac,
+__global__ void yee_march_fix_kernel(YeeArgs<T, ID> a, const uint32_t *__restrict__ off, const T *__restrict__ fac,
                                      const int32_t *__restrict__ port, int nterm, const FlatPort *__restrict__ prb,
                                      int nprb) {
   wait_prior_grid();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nterm) {
     T *f = a.Eout + off[t];
-    *f += fac[t] * a.u[port[t]];
+    *f += fac[t] * a.u[port ? port[t] : 0];
   } else if (t - nterm < nprb) {
     const FlatPort pe = prb[t - nterm];
     atomicAdd(&a.y[pe.port], (T)pe.w * a.Eout[pe.comp * a.nc + pe.cell]);
@@ -626,14 +626,20 @@ static fdtd_status ensure_fix(fdtd_grid *g, const YeeArgs<T, ID> &a, cudaStream_
       for (const FlatPort &pe : prb)
         disjoint &= !std::binary_search(uo.begin(), uo.end(), pe.comp * g->nc + pe.cell);
     }
-    if (unique && !uo.empty()) {
+    if (unique && !uo.empty() && 6 * g->nc <= (int64_t)UINT32_MAX) {
       g->nfix = (int)uo.size();
-      FDTD_CHECK(g->fix_off.alloc(uo.size() * sizeof(int64_t), s));
+      // 32-bit offsets (the grid is checked below 2^32 field values) and no
+      // port array on single-port grids: 8 bytes of term data per value
+      const std::vector<uint32_t> u32(uo.begin(), uo.end());
+      FDTD_CHECK(g->fix_off.alloc(u32.size() * sizeof(uint32_t), s));
       FDTD_CHECK(g->fix_fac.alloc(uf.size() * sizeof(T), s));
-      FDTD_CHECK(g->fix_port.alloc(up.size() * sizeof(int32_t), s));
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_off.ptr, uo.data(), uo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_off.ptr, u32.data(), u32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
       FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_fac.ptr, uf.data(), uf.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-      FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_port.ptr, up.data(), up.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      g->fix_port.release(s);
+      if (g->ports.size() > 1) {
+        FDTD_CHECK(g->fix_port.alloc(up.size() * sizeof(int32_t), s));
+        FDTD_CHECK_CUDA(cudaMemcpyAsync(g->fix_port.ptr, up.data(), up.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      }
       FDTD_CHECK_CUDA(cudaStreamSynchronize(s));
       g->fix_one = disjoint;
     }
@@ -725,7 +731,7 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
   if (g->nfix && g->fix_one) {  // gathered source terms and the probes in one launch
     const int nt = g->nfix + g->nflat_prb;
     FDTD_CHECK_CUDA(launch_dependent(yee_march_fix_kernel<T, ID>, dim3((nt + 255) / 256), dim3(256), s, a,
-                                     g->fix_off.as<const int64_t>(), g->fix_fac.as<const T>(),
+                                     g->fix_off.as<const uint32_t>(), g->fix_fac.as<const T>(),
                                      g->fix_port.as<const int32_t>(), g->nfix, g->flat_prb.as<const FlatPort>(),
                                      g->nflat_prb));
     FDTD_CHECK(after_launch("yee_march_fix_kernel"));
@@ -733,7 +739,7 @@ static fdtd_status launch_march_v(fdtd_grid *g, const void *u_row, void *y_row, 
   }
   if (g->nfix) {
     FDTD_CHECK_CUDA(launch_dependent(yee_march_fix_kernel<T, ID>, dim3((g->nfix + 255) / 256), dim3(256), s, a,
-                                     g->fix_off.as<const int64_t>(), g->fix_fac.as<const T>(),
+                                     g->fix_off.as<const uint32_t>(), g->fix_fac.as<const T>(),
                                      g->fix_port.as<const int32_t>(), g->nfix, g->flat_prb.as<const FlatPort>(), 0));
     FDTD_CHECK(after_launch("yee_march_fix_kernel"));
   } else if (g->nflat_src) {
