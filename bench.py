@@ -394,6 +394,11 @@ def schur_hbm_measure(F, W, hbm, peak_src):
     # the bench cavity's expansion arc (L = 2, fmax = 15 GHz, M = 1 + pi fmax dt0) on this grid's dt
     pts = SimpleNamespace(grid=wl.grid, L=2, M=1.0 + np.pi * 15e9 * dt0, fmax=15e9, include_center=True)
     out = schur_roofline(F, pts, grid, dt0, hbm, peak_src, reps=10, id_bytes=2)
+    # DRAM bytes per launch of this kernel on this grid from one ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum: 1.159 + 0.651 GB; the
+    # per-edge property arrays are the excess over the algorithmic bytes)
+    out["traffic"] = 1159e6 + 651e6
+    out["traffic_source"] = "profiles/schur_fused_metascreen_384x384x64.md"
     grid.close()
     return out
 
