@@ -30,6 +30,7 @@ fdtd_status after_launch(const char *name) {
   ++g_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, name);
+  if (kChecked && (e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, name);
   return FDTD_OK;
 }
 

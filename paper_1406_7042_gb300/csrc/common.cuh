@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -45,7 +46,33 @@ fdtd_status cuda_fail(cudaError_t e, const char *what);
     }                                          \
   } while (0)
 
-// After a kernel launch: count it and surface launch-configuration errors.
+// Checked build (-DFDTD_CHECKED, libfdtdmor_checked.so): every launch is
+// followed by a device synchronisation, so an asynchronous fault is reported
+// with the kernel that caused it; no CUDA graph is captured; and the stepping
+// kernels check the indices they take from the port lists, recording bit 16
+// of the grid's error flag (FDTD_ECUDA from fdtd_check) and skipping the
+// access instead of making it.
+#ifdef FDTD_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+inline bool graphs_off() { return kChecked || getenv("FDTDMOR_NO_GRAPH") != nullptr; }
+#ifdef __CUDACC__
+__device__ __forceinline__ bool dcheck(unsigned *err, bool ok) {
+#ifdef FDTD_CHECKED
+  if (!ok && err) atomicOr(err, 16u);
+  return ok;
+#else
+  (void)err;
+  (void)ok;
+  return true;
+#endif
+}
+#endif
+
+// After a kernel launch: count it and surface launch-configuration errors
+// (and, in the checked build, execution errors).
 fdtd_status after_launch(const char *name);
 void add_launches(int64_t n);  // kernel launches made by a graph replay
 

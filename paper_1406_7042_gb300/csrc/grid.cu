@@ -389,6 +389,10 @@ fdtd_status fdtd_check(fdtd_grid *g, fdtd_stream_t stream) {
       set_error("a bounded device-side wait of the stepping kernel gave up; the fields are not valid");
       return FDTD_ETIMEOUT;
     }
+    if (h & 16u) {
+      set_error("an index check of the checked build failed (a port-list entry outside the grid); the fields are not valid");
+      return FDTD_ECUDA;
+    }
     set_error("the field watchdog fired: %s", (h & 4u) ? "NaN or Inf in the fields" : "field energy grew beyond the limit");
     return FDTD_EUNSTABLE;
   }

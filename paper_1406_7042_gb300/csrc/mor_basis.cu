@@ -1584,7 +1584,7 @@ struct BasisBuilder {
       return after_launch("cocg_edge_kernel");
     };
     const int poll = 16;
-    if (!cocg_graph && !getenv("FDTDMOR_NO_GRAPH")) {
+    if (!cocg_graph && !graphs_off()) {
       if (!cap) FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       const int64_t before = fdtd_launch_count(0);
       FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -1775,7 +1775,7 @@ struct BasisBuilder {
     const int poll = 16;
     cudaGraphExec_t block = nullptr;
     int64_t block_launches = 0;
-    if (!getenv("FDTDMOR_NO_GRAPH")) {
+    if (!graphs_off()) {
       if (!cap) FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       const int64_t before = fdtd_launch_count(0);
       FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));

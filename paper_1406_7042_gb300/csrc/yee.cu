@@ -386,7 +386,7 @@ fdtd_status yee_run(fdtd_grid *g, double dt, int64_t nsteps, const void *u, void
     return launch_yee(g, ur, yr, kchunk, s);
   };
   int64_t n = 0;
-  if (nsteps > 2 * kGraphSteps && !getenv("FDTDMOR_NO_GRAPH")) {
+  if (nsteps > 2 * kGraphSteps && !graphs_off()) {
     // one direct step first (lazily built device tables are made outside any
     // capture), then whole chunks as replays of a captured graph: u rows are
     // staged into a fixed buffer before each replay and y rows copied out

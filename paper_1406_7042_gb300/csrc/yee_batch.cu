@@ -252,7 +252,7 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
     return after_launch("batch_advance_kernel");
   };
   int64_t n = 0;
-  if (nsteps >= 2 * kBatchGraphSteps && !getenv("FDTDMOR_NO_GRAPH")) {
+  if (nsteps >= 2 * kBatchGraphSteps && !graphs_off()) {
     FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     const int64_t before = fdtd_launch_count(0);
     FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));

@@ -27,6 +27,7 @@ struct YeeArgs {
   const int32_t *__restrict__ prb_ptr;
   const PortEntry *__restrict__ prb;
   T *__restrict__ y;           // row of this step: y[probe]
+  unsigned *err = nullptr;     // the grid's error flag (index checks of the checked build)
 };
 
 template <typename T>

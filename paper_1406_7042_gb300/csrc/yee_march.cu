@@ -492,7 +492,7 @@ template <typename T, typename ID, bool HOMOG_H>
 __global__ void yee_march_src_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ src, int nsrc) {
   wait_prior_grid();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nsrc) {
+  if (q < nsrc && dcheck(a.err, src[q].cell >= 0 && src[q].cell < a.nc && src[q].comp >= 0 && src[q].comp < 3)) {
     const FlatPort f = src[q];
     const T u = a.u[f.port];
     src_terms<T, ID, HOMOG_H>(a, f, [&](int64_t off, T fac) { atomicAdd(a.Eout + off, fac * u); });
@@ -526,10 +526,12 @@ __global__ void yee_march_fix_kernel(YeeArgs<T, ID> a, const uint32_t *__restric
   wait_prior_grid();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nterm) {
+    if (!dcheck(a.err, off[t] < 6 * a.nc)) return;
     T *f = a.Eout + off[t];
     *f += fac[t] * a.u[port ? port[t] : 0];
   } else if (t - nterm < nprb) {
     const FlatPort pe = prb[t - nterm];
+    if (!dcheck(a.err, pe.cell >= 0 && pe.cell < a.nc && pe.comp >= 0 && pe.comp < 3)) return;
     atomicAdd(&a.y[pe.port], (T)pe.w * a.Eout[pe.comp * a.nc + pe.cell]);
   }
   allow_next_grid();
@@ -540,7 +542,7 @@ template <typename T, typename ID>
 __global__ void yee_march_prb_kernel(YeeArgs<T, ID> a, const FlatPort *__restrict__ prb, int nprb) {
   wait_prior_grid();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nprb) {
+  if (q < nprb && dcheck(a.err, prb[q].cell >= 0 && prb[q].cell < a.nc && prb[q].comp >= 0 && prb[q].comp < 3)) {
     const FlatPort f = prb[q];
     atomicAdd(&a.y[f.port], (T)f.w * a.Eout[f.comp * a.nc + f.cell]);
   }

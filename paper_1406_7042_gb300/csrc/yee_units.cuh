@@ -246,6 +246,7 @@ __device__ __forceinline__ void e_unit(const YeeArgs<T, ID> &a, const ID *__rest
     for (int q = s0 + tid; q < s1; q += LTX * LTY) {
       const PortEntry pe = a.src[q];
       if (pe.k < k0 || pe.k >= k1 || pe.lx >= LTX * VW || pe.ly >= LTY) continue;
+      if (!dcheck(a.err, pe.comp >= 0 && pe.comp < 3 && pe.lx >= 0 && pe.ly >= 0 && pe.port >= 0)) continue;
       const int si = bx * LTX * VW + pe.lx, sj = by * LTY + pe.ly, k = pe.k;
       if (si >= nx || sj >= ny) continue;
       const int64_t n = k * plane + (int64_t)sj * nx + si;
@@ -355,6 +356,7 @@ __device__ __forceinline__ void h_unit(const YeeArgs<T, ID> &a, int bx, int by, 
   for (int q = p0 + tid; q < p1; q += LTX * LTY) {
     const PortEntry pe = a.prb[q];
     if (pe.k < k0 || pe.k >= k1) continue;
+    if (!dcheck(a.err, pe.comp >= 0 && pe.comp < 3 && pe.lx >= 0 && pe.ly >= 0 && pe.port >= 0)) continue;
     const int si = bx * LTX * VW + pe.lx, sj = by * LTY + pe.ly;
     if (si >= nx || sj >= ny) continue;
     atomicAdd(&a.y[pe.port], (T)pe.w * ldf<COH>(a.Eout + pe.comp * nc + pe.k * plane + (int64_t)sj * nx + si));
@@ -412,6 +414,7 @@ inline YeeArgs<T, ID> split_args(fdtd_grid *g) {
   a.prb_ptr = g->lists.prb_ptr.as<int32_t>();
   a.prb = g->lists.prb.as<PortEntry>();
   a.y = nullptr;
+  a.err = g->errflag.as<unsigned>();
   return a;
 }
 

@@ -17,7 +17,11 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfdtdmor.so")
+# FDTDMOR_CHECKED=1 loads the checked build (paper_1406_7042_gb300.build with
+# checked=True): a synchronisation after every launch, no CUDA graphs, index
+# checks of the port lists; for debugging, not for timing.
+LIB_PATH = os.path.join(_HERE, "libfdtdmor_checked.so" if os.environ.get("FDTDMOR_CHECKED") == "1"
+                        else "libfdtdmor.so")
 
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ENOCONV, FDTD_EUNSTABLE, FDTD_ETIMEOUT = range(7)
 FDTD_F64, FDTD_F32 = 0, 1

@@ -25,3 +25,15 @@ def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
         assert "not built" in str(e)
     else:
         raise AssertionError("loading a missing library must raise")
+
+
+def test_checked_build_exports_every_declared_symbol():
+    """The -DFDTD_CHECKED variant (synchronised launches, no graphs, index
+    checks) builds on its own objects and exports the same C ABI."""
+    import ctypes
+    from paper_1406_7042_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libfdtdmor_checked.so") and path != F.LIB_PATH
+    L = ctypes.CDLL(path)
+    missing = [n for n in F.declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
