@@ -333,6 +333,8 @@ def run_ours(args):
                                            ("workload", "grid", "Mcell_updates_per_s", "frac_of_measured_hbm")}
         if args.mor:
             line["schur_roofline_hbm"] = schur_hbm_measure(F, W, hbm, peak_src)
+    if rank == 0 and args.adjoint:
+        line["adjoint"] = adjoint_measure(F, W)
     if rank == 0 and args.batch:
         line["batch"] = batch_measure(F, W)
         line["batch"]["reduction"] = batch_reduce_measure(F, W)
@@ -808,6 +810,36 @@ def hbm_grid_measure(F, W, hbm, nsteps=200):
             "bytes_per_cell": bytes_per_cell}
 
 
+def adjoint_measure(F, W):
+    """The adjoint form on the full-size metascreen (384x384x64, 4097
+    materials, 2048 FP32 steps, default sqrt(T) checkpoints): gradient of the
+    focal-probe energy with respect to every pixel's eps_r (fdtd_adjoint)
+    against the plain FP32 forward run of the same steps on the same GPU."""
+    import torch
+    wl = W.metascreen_workload()
+    g = wl.grid
+    grid = F.Grid(g, "f32")
+    dt = wl.s_ref * grid.cfl_dt()
+    n = wl.nsteps_ref
+    u = torch.tensor(W.excitation(g, wl.f0, wl.bw, dt, n), dtype=torch.float32, device="cuda")
+    y = grid.step(dt, u, reset=True)
+    y, t_f = _timed(lambda: grid.step(dt, u, reset=True))
+    gy = (2.0 * dt) * y
+    grid.adjoint(dt, u[:64].contiguous(), gy[:64].contiguous(), per_cell=False)
+    (_, gm), t_a = _timed(lambda: grid.adjoint(dt, u, gy, per_cell=False))
+    ok = bool(torch.isfinite(gm).all())
+    ncp = int(math.ceil(math.sqrt(n)))
+    seg = -(-n // ncp)
+    # K full-state checkpoints plus the c + 1 E fields of one segment
+    mem_mb = (ncp * 6 + (seg + 1) * 3) * g.ncells * 4 / 1e6
+    grid.close()
+    return {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "steps": n, "pixels": int(g.nmat) - 2,
+            "forward_ms": round(t_f, 1), "adjoint_ms": round(t_a, 1), "adjoint_over_forward": round(t_a / t_f, 2),
+            "checkpoints": ncp, "checkpoint_mb": round(mem_mb, 1), "gradient_finite": ok,
+            "note": "adjoint = forward with checkpoints + recomputation between them + adjoint leap-frog "
+                    "+ per-material gradient accumulation"}
+
+
 def reduced_run_measure(F, W, q_list=(40, 80, 200, 400), nsteps=20000):
     """Reduced leap-frog (mor_run) microseconds per step for FP32 models of
     order q (random SPD-projected models are not needed: the step matrices of
@@ -891,6 +923,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hbm-grid", type=int, default=1)
     ap.add_argument("--batch", type=int, default=1, help="measure the batched cavity workload")
+    ap.add_argument("--adjoint", type=int, default=1, help="time the adjoint gradient on the full metascreen")
+    ap.add_argument("--only-adjoint", action="store_true")
     ap.add_argument("--tensor", type=int, default=1, help="tensor-core Gram throughput and the precision study")
     ap.add_argument("--mor", type=int, default=1, help="include the reduction stages in the bench step")
     ap.add_argument("--study", type=int, default=1, help="reduce+run at other settings (q, M, absorbers)")
@@ -942,6 +976,11 @@ def main():
         from paper_1406_7042_gb300 import fdtdmor as F
         from paper_1406_7042_gb300 import workloads as W
         print(json.dumps({"only_run": reduced_run_measure(F, W)}))
+        return 0
+    if args.only_adjoint:
+        from paper_1406_7042_gb300 import fdtdmor as F
+        from paper_1406_7042_gb300 import workloads as W
+        print(json.dumps({"only_adjoint": adjoint_measure(F, W)}))
         return 0
     if args.only_batch:
         from paper_1406_7042_gb300 import fdtdmor as F
