@@ -62,7 +62,7 @@ __global__ void field_energy_kernel(const T *__restrict__ f, int64_t half, doubl
   }
 }
 
-__global__ void watchdog_judge_kernel(const double *__restrict__ acc, double growth, unsigned *err) {
+__global__ void watchdog_decide_kernel(const double *__restrict__ acc, double growth, unsigned *err) {
   const double before = acc[0], after = acc[1];
   if (!isfinite(after)) atomicOr(err, 4u);
   else if (growth > 0 && before > 0 && after > growth * before) atomicOr(err, 8u);
@@ -93,8 +93,8 @@ fdtd_status watchdog_after(fdtd_grid *g, const void *u, int reset_fields, cudaSt
   double *acc = g->wd_acc.as<double>();
   FDTD_CHECK(field_energy(g, acc + 1, s));
   const double growth = (g->wd_growth > 0 && source_free(g, u) && !reset_fields) ? g->wd_growth : 0.0;
-  watchdog_judge_kernel<<<1, 1, 0, s>>>(acc, growth, g->errflag.as<unsigned>());
-  FDTD_CHECK(after_launch("watchdog_judge_kernel"));
+  watchdog_decide_kernel<<<1, 1, 0, s>>>(acc, growth, g->errflag.as<unsigned>());
+  FDTD_CHECK(after_launch("watchdog_decide_kernel"));
   if (!g->wd_sync) return FDTD_OK;
   unsigned h = 0;
   FDTD_CHECK_CUDA(cudaMemcpyAsync(&h, g->errflag.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
