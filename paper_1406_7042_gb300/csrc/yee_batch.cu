@@ -9,6 +9,7 @@
 // a grid's input and output buffers follow its step parity, so a captured
 // chunk of steps replays without host changes.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -214,19 +215,25 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
   DevBuf step;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> gstr;  // per-group branches of the captured step
+  std::vector<cudaEvent_t> gev;    // fork event, then one join event per group
   struct Cleanup {
     std::vector<BatchGroup *> &gl;
     DevBuf &step;
     cudaStream_t &cap;
     cudaGraphExec_t &exec;
+    std::vector<cudaStream_t> &gstr;
+    std::vector<cudaEvent_t> &gev;
     cudaStream_t s;
     ~Cleanup() {
       for (auto *b : gl) { b->release(s); delete b; }
       step.release(s);
       if (exec) cudaGraphExecDestroy(exec);
       if (cap) cudaStreamDestroy(cap);
+      for (auto x : gstr) cudaStreamDestroy(x);
+      for (auto e : gev) cudaEventDestroy(e);
     }
-  } cleanup{gl, step, cap, exec, s};
+  } cleanup{gl, step, cap, exec, gstr, gev, s};
   for (auto &kv : groups) {
     const int prec = std::get<0>(kv.first), idb = std::get<1>(kv.first), hh = std::get<2>(kv.first),
               vw = std::get<3>(kv.first), pre = std::get<4>(kv.first);
@@ -251,13 +258,43 @@ static fdtd_status step_batched(fdtd_grid *const *grids, int ngrids, const doubl
     FDTD_CHECK_CUDA(launch_dependent(batch_advance_kernel, dim3(1), dim3(32), st, step.as<long long>()));
     return after_launch("batch_advance_kernel");
   };
+  // In the captured graph the groups (different grids, so independent until
+  // the step counter advances) run as parallel branches: each group's E and
+  // H launches on a stream of its own, forked from and joined back into the
+  // capture stream around the counter's advance.
+  auto one_step_branched = [&](cudaStream_t st) -> fdtd_status {
+    const int ng = (int)gl.size();
+    FDTD_CHECK_CUDA(cudaEventRecord(gev[0], st));
+    for (int q = 0; q < ng; ++q) {
+      FDTD_CHECK_CUDA(cudaStreamWaitEvent(gstr[q], gev[0], 0));
+      FDTD_CHECK(gl[q]->launch_e(gstr[q], sp));
+      FDTD_CHECK(gl[q]->launch_h(gstr[q], sp));
+      FDTD_CHECK_CUDA(cudaEventRecord(gev[1 + q], gstr[q]));
+      FDTD_CHECK_CUDA(cudaStreamWaitEvent(st, gev[1 + q], 0));
+    }
+    FDTD_CHECK_CUDA(launch_dependent(batch_advance_kernel, dim3(1), dim3(32), st, step.as<long long>()));
+    return after_launch("batch_advance_kernel");
+  };
   int64_t n = 0;
   if (nsteps >= 2 * kBatchGraphSteps && !graphs_off()) {
     FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const bool branched = gl.size() > 1 && !(getenv("FDTDMOR_BATCH_SERIAL") && atoi(getenv("FDTDMOR_BATCH_SERIAL")));
+    if (branched) {
+      for (size_t q = 0; q < gl.size(); ++q) {
+        cudaStream_t x;
+        FDTD_CHECK_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        gstr.push_back(x);
+      }
+      for (size_t q = 0; q <= gl.size(); ++q) {
+        cudaEvent_t e;
+        FDTD_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        gev.push_back(e);
+      }
+    }
     const int64_t before = fdtd_launch_count(0);
     FDTD_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     fdtd_status st = FDTD_OK;
-    for (int t = 0; t < kBatchGraphSteps && st == FDTD_OK; ++t) st = one_step(cap);
+    for (int t = 0; t < kBatchGraphSteps && st == FDTD_OK; ++t) st = branched ? one_step_branched(cap) : one_step(cap);
     const int64_t per_replay = fdtd_launch_count(0) - before;
     add_launches(-per_replay);
     cudaGraph_t graph = nullptr;
