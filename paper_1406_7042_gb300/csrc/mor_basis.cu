@@ -420,11 +420,15 @@ __global__ void __launch_bounds__(MB) e_from_h_kernel(OpArgs<T> a, const cplx<T>
 // outside the grid contribute zero, as in curl_h3.
 // VDOT: partials of (p, q)_V and, with tickets, alpha = rho / (p, q)_V by
 // the last CTA of each right-hand side.  Grid: (RHS groups, tiles, z chunks).
+// The COCG form (FP32, dot terms, one RHS per thread) is held to 64
+// registers for three CTAs per SM, without spills: more warps in flight,
+// 2.84 against 2.99 s for the q = 200 basis of the 64^3 cavity (four CTAs
+// spill: 2.85 s).
 constexpr int kSX = 32, kSY = 8;
 constexpr int kSThreads = 32 * (kSY + 2);
 
 template <typename T, bool VDOT, int NB>
-__global__ void __launch_bounds__(kSThreads, 2) schur_fused_kernel(OpArgs<T> a, int nb, const cplx<T> *__restrict__ p,
+__global__ void __launch_bounds__(kSThreads, (VDOT && NB == 1 && sizeof(T) == 4) ? 3 : 2) schur_fused_kernel(OpArgs<T> a, int nb, const cplx<T> *__restrict__ p,
                                                                    cplx<T> *__restrict__ q, int64_t stride, int ntx,
                                                                    int zchunk, CgsScal *__restrict__ sc,
                                                                    double *__restrict__ partials,
