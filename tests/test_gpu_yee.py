@@ -323,3 +323,24 @@ def test_tensor_maps_follow_a_new_grid_at_reused_addresses(monkeypatch, kernel):
     for c in range(6):
         assert _rel(fg[c], fo[c]) <= 1e-4, c
     assert _rel(yg, yo) <= TOL_F32_PROBE
+
+
+@pytest.mark.parametrize("case", ["gathered", "probe_on_source", "two_ports_one_edge"])
+def test_march_source_terms_against_oracle(case):
+    """The fused z-march form applies sources and probes after its pass from
+    terms gathered per field value: in one launch (case "gathered"), with the
+    probes in a second launch when a probe edge carries a source term, and
+    with the atomic source kernel when two ports drive one edge.  FP64 fields
+    and probes against the oracle."""
+    g = ragged_grid(nx=24, ny=14, nz=10, seed=77)
+    p0 = g.ports[0]
+    if case == "probe_on_source":
+        g.probes.append(W.Port.point(p0.comp, int(p0.i[0]), int(p0.j[0]), int(p0.k[0]), 0.7))
+    elif case == "two_ports_one_edge":
+        g.ports.append(W.Port.point(p0.comp, int(p0.i[0]), int(p0.j[0]), int(p0.k[0]), -0.4))
+    dt = 0.95 * yee.cfl_dt(g)
+    u = drive(g, dt, 120)
+    _, yg, fg = _run_gpu(g, "f64", dt, u, kernel="march")
+    _, yo, fo = _run_oracle(g, dt, u)
+    assert np.max(np.abs(fg - fo)) <= TOL_F64 * np.abs(fo).max()
+    assert np.max(np.abs(yg - yo)) <= TOL_F64 * np.abs(yo).max()
