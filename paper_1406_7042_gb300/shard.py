@@ -23,7 +23,9 @@ only, and the probe outputs are the sum over ranks (one all-reduce per run).
 
 Row-partitioned Gram and projection sums (Sec. II-C, Eq. (R_and_Freduced)):
 a rank holding the rows of its slab forms its part of G = A^T diag(w) B
-(mor_gram or mor_project on the local rows) and allreduce_sum adds the parts.
+(mor_gram or mor_project on the local rows) and allreduce_sum adds the parts;
+cgs2_deflate_rows orthonormalises row-partitioned pools the same way, one
+all-reduce per Gram-Schmidt pass and per norm.
 
 The local stepping is delegated to an object with step(u_rows) -> y_rows,
 planes(k0, nk) and set_planes(k0, f) over (6, nk, ny, nx) arrays: GridSlab
@@ -161,6 +163,44 @@ def allreduce_sum(t, group=None):
     import torch.distributed as dist
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t
+
+
+def cgs2_deflate_rows(pool_rows, defl_tol: float, gram: Callable = None, group=None):
+    """CGS2 with deflation (Sec. II-C: the orthonormalisation of the SPRIM
+    pools) over row-partitioned vectors.  This rank holds the same rows of
+    every pool vector (pool_rows: list of 1-D tensors) and of the basis it
+    builds.  Each of the two passes against the basis forms the rank's part of
+    the coefficients V_r^T w_r and adds the parts over the ranks with one
+    all-reduce, then updates w_r -= V_r h locally; each norm is a local sum of
+    squares added by one all-reduce.  All ranks see the same reduced sums and
+    so keep or drop the same vectors: a vector whose norm after the passes is
+    below defl_tol times its norm before is dropped.  gram(V_r, w_r) returns
+    V_r^T w_r (a matmul on the tensors' device by default; mor_gram for rows
+    held on a GPU).  Returns the rank's rows of the basis (n_r x q tensor)."""
+    import torch
+    gram = gram or (lambda V, w: V.transpose(0, 1) @ w)
+
+    def norm(w):
+        return float(allreduce_sum((w * w).sum().reshape(1), group)[0]) ** 0.5
+
+    cols = []
+    for p in pool_rows:
+        w = p.clone()
+        n0 = norm(w)
+        if n0 == 0:
+            continue
+        if cols:
+            V = torch.stack(cols, dim=1)
+            for _ in range(2):
+                h = allreduce_sum(gram(V, w), group)
+                w = w - V @ h
+        n1 = norm(w)
+        if n1 < defl_tol * n0:
+            continue
+        cols.append(w / n1)
+    if not cols:
+        return torch.zeros((pool_rows[0].shape[0], 0), dtype=pool_rows[0].dtype, device=pool_rows[0].device)
+    return torch.stack(cols, dim=1)
 
 
 class GridSlab:

@@ -103,6 +103,25 @@ def _gram_worker(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
+def _cgs2_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(9)
+        n = 301
+        pool = [rng.standard_normal(n) for _ in range(7)]
+        pool.insert(3, 0.5 * pool[0] - 2.0 * pool[2])             # dependent: deflated
+        pool.insert(6, pool[1] + 1e-3 * rng.standard_normal(n))    # nearly dependent: kept at 1e-8
+        pool.append(np.zeros(n))                                    # zero: skipped
+        ref = mor.cgs2_deflate(pool, 1e-8)
+        r0, r1 = shard.row_range(n, world, rank)
+        V = shard.cgs2_deflate_rows([torch.tensor(p[r0:r1]) for p in pool], 1e-8).numpy()
+        ok = V.shape[1] == ref.shape[1] and np.allclose(V, ref[r0:r1], rtol=0, atol=1e-11)
+        np.save(os.path.join(out_dir, f"c{rank}.npy"), np.array([ok, V.shape[1], ref.shape[1]]))
+    finally:
+        dist.destroy_process_group()
+
+
 def _free_port():
     with socket.socket() as sck:
         sck.bind(("127.0.0.1", 0))
@@ -144,3 +163,15 @@ def test_slab_ranges_and_local_grids():
         assert prev == g.nz
     with pytest.raises(ValueError):
         shard.slab_range(3, 4, 0)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_partitioned_cgs2_matches_oracle(world, tmp_path):
+    """CGS2 with deflation on row-partitioned pools (one all-reduce per pass
+    and per norm) keeps the same vectors as the oracle's cgs2_deflate on the
+    whole vectors, and each rank holds those rows of the same basis."""
+    import torch.multiprocessing as mp
+    mp.spawn(_cgs2_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        ok, q, qref = np.load(tmp_path / f"c{r}.npy")
+        assert ok and q == qref == 8, (r, q, qref)
