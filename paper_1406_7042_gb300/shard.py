@@ -25,7 +25,8 @@ Row-partitioned Gram and projection sums (Sec. II-C, Eq. (R_and_Freduced)):
 a rank holding the rows of its slab forms its part of G = A^T diag(w) B
 (mor_gram or mor_project on the local rows) and allreduce_sum adds the parts;
 cgs2_deflate_rows orthonormalises row-partitioned pools the same way, one
-all-reduce per Gram-Schmidt pass and per norm.
+all-reduce per Gram-Schmidt pass and per norm, and cocg_rows solves a
+row-partitioned shifted system with one all-reduce per inner product.
 
 The local stepping is delegated to an object with step(u_rows) -> y_rows,
 planes(k0, nk) and set_planes(k0, f) over (6, nk, ny, nx) arrays: GridSlab
@@ -201,6 +202,53 @@ def cgs2_deflate_rows(pool_rows, defl_tol: float, gram: Callable = None, group=N
     if not cols:
         return torch.zeros((pool_rows[0].shape[0], 0), dtype=pool_rows[0].dtype, device=pool_rows[0].device)
     return torch.stack(cols, dim=1)
+
+
+def cocg_rows(apply_rows: Callable, b_rows, pinv_rows, tol: float, maxit: int, group=None):
+    """Preconditioned COCG on a row-partitioned complex symmetric system
+    (the shifted Schur-complement solves of Sec. IV-B): this rank holds rows
+    of b, of the diagonal preconditioner pinv and of every iterate;
+    apply_rows(p_rows) returns this rank's rows of S p (it exchanges what the
+    operator needs from other ranks).  The unconjugated products (p, S p) and
+    (r, P r) and the residual norm are local sums added by one all-reduce
+    each; the vector updates are local.  Stops at ||r|| <= tol ||b|| or
+    maxit.  Returns (x_rows, iterations, relative residual)."""
+    import torch
+
+    def reduce(*vals):
+        t = torch.tensor([float(v) for v in vals], dtype=torch.float64)
+        return allreduce_sum(t, group).tolist()
+
+    def udot(a, b):  # sum a_i b_i, unconjugated
+        v = (a * b).sum()
+        return complex(*reduce(v.real, v.imag))
+
+    x = torch.zeros_like(b_rows)
+    r = b_rows.clone()
+    bn = reduce((b_rows.abs() ** 2).sum())[0] ** 0.5
+    if bn == 0:
+        return x, 0, 0.0
+    z = pinv_rows * r
+    p = z.clone()
+    rho = udot(r, z)
+    rel = 1.0
+    it = 0
+    while it < maxit:
+        q = apply_rows(p)
+        alpha = rho / udot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        z = pinv_rows * r
+        v = (r * z).sum()
+        re, im, rn2 = reduce(v.real, v.imag, (r.abs() ** 2).sum())
+        rel = rn2 ** 0.5 / bn
+        if rel <= tol:
+            break
+        rho_new = complex(re, im)
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    return x, it, rel
 
 
 class GridSlab:
