@@ -138,8 +138,10 @@ FDTD_API double fdtd_cfl_dt(const fdtd_grid *grid);
  * recomputed; in FP32 with 4 cells per thread the plane inputs are staged in
  * shared memory by TMA three planes ahead (rows of the fields and of the
  * material map 16-byte aligned: nx a multiple of 4, and of 16 with uint8
- * material ids); sources and probes follow in two small launches (the step
- * is linear).  A staged wait that gives up sets the flag fdtd_check reports. */
+ * material ids); sources and probes follow in one small launch (the step is
+ * linear; the sources' terms are gathered once per dt into one term per
+ * field value and port).  A staged wait that gives up sets the flag
+ * fdtd_check reports. */
 typedef enum {
   FDTD_KERNEL_AUTO = 0,
   FDTD_KERNEL_PERSIST = 1,
@@ -219,7 +221,9 @@ FDTD_API fdtd_status fdtd_grid_set_wait_limit(fdtd_grid *grid, long long polls);
  * FDTD_ETIMEOUT if a bounded device-side wait of an earlier fdtd_step gave up
  * (an mbarrier wait of a TMA-staged form, or a completion-counter wait of the
  * dataflow form; the fields are then undefined), FDTD_EUNSTABLE if the field
- * watchdog fired (fdtd_grid_set_watchdog). */
+ * watchdog fired (fdtd_grid_set_watchdog), and, in the checked build
+ * (libfdtdmor_checked.so, compiled with -DFDTD_CHECKED), FDTD_ECUDA if a
+ * port-list index check of a stepping kernel failed (the access was skipped). */
 FDTD_API fdtd_status fdtd_check(fdtd_grid *grid, fdtd_stream_t stream);
 
 /* Copy the six field arrays (Ex, Ey, Ez, Hx, Hy, Hz, each nx*ny*nz of the
@@ -376,9 +380,13 @@ FDTD_API fdtd_status mor_opts_default(mor_opts *opts);
  * z_l = M exp(j 2 pi (l/L) fmax dt0), l = 0..L (conjugate points implied), a
  * block-Arnoldi chain of k = q/((2L+1) m) block moments
  * v_0 = A_l^{-1} B, v_j = A_l^{-1} (R+F) v_{j-1}, A_l = z_l (R+F) - (R-F), each
- * shifted solve by conjugate gradient squared on the Schur complement
- * A11 - A12 A22^{-1} A21 (Eqs. (reduced_linear_system_solution1/2)), Jacobi
- * preconditioned, to a normalised residual <= tol; then Re/Im of every
+ * shifted solve an iterative solve on the Schur complement
+ * A11 - A12 A22^{-1} A21 (Eqs. (reduced_linear_system_solution1/2)) to a
+ * normalised residual <= tol, all points and ports of one moment as the
+ * right-hand sides of one solve (opts->solver: conjugate gradient squared
+ * with Jacobi preconditioning by default on FDTD_F64 grids, COCG with the
+ * gradient-corrected preconditioner and FP64 refinement on FDTD_F32 grids,
+ * see mor_solver above); then Re/Im of every
  * chain vector is split into its E and H parts and each pool is
  * orthonormalised with CGS2 and deflation -> V1 (3nc x q1), V2 (3nc x q2).
  * Returns FDTD_ENOCONV if a solve hit maxit (the basis is still returned). */
