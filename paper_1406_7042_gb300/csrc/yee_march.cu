@@ -21,8 +21,11 @@
 // DRAM sees each field value read once and written once per step (the 48 B
 // per cell of the fused form, plus the material map); the halo row's and
 // chunk tops' reads come mostly from L2.  Sources and probes are applied
-// afterwards by two small kernels: the step is linear, so a source's effect on
-// this step's H is -Db curlE(dE) on the four H edges around the source edge.
+// afterwards by one small kernel: the step is linear, so a source's effect on
+// this step's H is -Db curlE(dE) on the four H edges around the source edge;
+// these terms are gathered once per dt into one term per field value and port
+// (ensure_fix), and the probes share the launch when no probe edge carries a
+// term (else an atomic source kernel and a probe kernel follow).
 #include <algorithm>
 #include <cstring>
 #include <vector>
