@@ -12,7 +12,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import sys
-from typing import List, Optional, Sequence
+from typing import List, Optional
 
 import numpy as np
 
